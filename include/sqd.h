@@ -1,0 +1,245 @@
+/*
+ * sqd.h -- C ABI of the GB300 (sm_103a) library for the hot path of
+ * sample-based quantum diagonalisation (SQD), arXiv 2601.16169.
+ *
+ * The method (Sections I-II): sampled electron configurations are filtered
+ * into sets of alpha strings I_a and beta strings I_b; the Hamiltonian is
+ * diagonalised on span{|I_a I_b>} by the Davidson method, whose cost is the
+ * matrix-free product sigma = H C (96.5% of an iteration, Section VI) built
+ * from one- and two-electron integrals through the Slater-Condon rules.
+ *
+ * Conventions used by every call
+ * ------------------------------
+ *  - Strings are uint64_t, bit k set = spatial orbital k occupied;
+ *    norb <= 64.  String sets are sorted ascending and free of duplicates.
+ *  - h is norb*norb doubles, h[p*norb+q] = h_pq; V is norb^4 doubles in
+ *    chemist notation, V[((p*norb+q)*norb+r)*norb+s] = (pq|rs).  Both must
+ *    be real-symmetric: h_pq = h_qp and V 8-fold symmetric (checked to
+ *    1e-10 relative, else SQD_EINVAL).
+ *  - H = E_core + sum_{pq,s} h_pq a+_{ps} a_{qs}
+ *        + 1/2 sum_{pqrs,st} (pq|rs) a+_{ps} a+_{rt} a_{st} a_{qs}.
+ *  - A determinant |I_a I_b> is the alpha-block-first product
+ *    prod_{k in I_a} a+_{k,alpha} prod_{l in I_b} a+_{l,beta} |0>, both
+ *    products in ascending orbital order.  Its index is ia * n_beta + ib,
+ *    so a vector C is an n_alpha x n_beta row-major matrix (Section IV:
+ *    work is threaded over the combined alpha x beta index space).
+ *  - Pointers named d_* are device memory owned by the caller (e.g. torch
+ *    tensors), h_* are host memory owned by the caller.  Opaque objects
+ *    (sqd_ctx, sqd_tables) are owned by the library.
+ *  - Every call returns an sqd_status; nothing aborts and no exception
+ *    crosses the ABI.  On error, sqd_last_error(ctx) describes it.
+ *  - Calls are enqueued on the context's stream.  Calls that return host
+ *    scalars (sqd_build_strings, sqd_excitation_tables, sqd_davidson,
+ *    sqd_tables_export) synchronise that stream before returning.
+ *  - Calls on one context must not run concurrently from several threads.
+ */
+#ifndef SQD_H
+#define SQD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sqd_ctx sqd_ctx;
+typedef struct sqd_tables sqd_tables;
+
+typedef enum {
+    SQD_OK = 0,
+    SQD_EINVAL = -1,        /* invalid argument */
+    SQD_ENOMEM = -2,        /* device allocation failed */
+    SQD_ECUDA = -3,         /* CUDA runtime error */
+    SQD_ENOTCONVERGED = -4, /* Davidson hit max_iter; best estimate returned */
+    SQD_EBREAKDOWN = -5,    /* Davidson basis could not be extended */
+    SQD_ETIMEOUT = -6       /* reserved */
+} sqd_status;
+
+/* ------------------------------------------------------------- context -- */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a
+ * cudaStream_t owned by the caller (NULL = the legacy default stream); all
+ * work of the context is enqueued on it. */
+int sqd_create(sqd_ctx **ctx, int device, void *cuda_stream);
+
+/* Replace the context's stream (caller-owned). */
+int sqd_set_stream(sqd_ctx *ctx, void *cuda_stream);
+
+/* Free the context (not the tables created with it: free those first). */
+void sqd_destroy(sqd_ctx *ctx);
+
+/* Text of the last error on this context ("" if none).  Owned by ctx. */
+const char *sqd_last_error(const sqd_ctx *ctx);
+
+/* Library version string, e.g. "sqd-gb300 0.1". */
+const char *sqd_version(void);
+
+/* -------------------------------------------- a1: string-set filtering -- */
+
+/*
+ * Filter sampled configurations into a string set (Sections I and V-A: the
+ * sampled configurations are filtered on the classical side; strings are
+ * one 64-bit word each, as with bit_length = norb in Section IV-A).
+ *
+ * d_raw[0..n_raw): raw strings (device).  Keeps those with exactly `nelec`
+ * bits set and no bit at or above `norb`, sorts them ascending and removes
+ * duplicates into d_out (device, capacity >= n_raw; may equal d_raw).
+ * *n_out (host) receives the number of strings written.
+ * Errors: SQD_EINVAL for norb outside [1, 64], nelec outside [0, norb],
+ * n_raw < 0 or NULL pointers with n_raw > 0.
+ */
+int sqd_build_strings(sqd_ctx *ctx, const uint64_t *d_raw, int64_t n_raw,
+                      int norb, int nelec, uint64_t *d_out, int64_t *n_out);
+
+/* ---------------------------------- a2-a4: excitation tables, diagonal -- */
+
+/*
+ * Build the excitation lists of both string sets and everything sigma needs
+ * (Sections II and V-A: per-string excitation lists flattened into
+ * offset + entry arrays; the integrals copied to the device once,
+ * Section V-C).  The library copies strings and integrals; the caller's
+ * buffers may be freed afterwards.
+ *
+ *   single entry of string I: target J = I - q + p (J in the set),
+ *     p = orbital created, q = orbital annihilated,
+ *     sign = <J| a+_p a_q |I> = (-1)^(number of occupied orbitals of I
+ *     strictly between p and q), val = <I|H_s|J>;
+ *   double entry of string I: target J = I - i - j + a + b, i < j, a < b,
+ *     sign = <J| a+_a a+_b a_j a_i |I>, val = <I|H_s|J>;
+ * H_s being the one-spin Hamiltonian (h plus the same-spin part of V).
+ * Entries of a row are sorted by target index.
+ *
+ * d_alpha / d_beta: sorted unique string sets (device); they may be the same
+ * buffer, in which case one table serves both spins.  nalpha_e / nbeta_e are
+ * the electron counts of the sets (checked).  d_h, d_V as in the
+ * conventions (device).  *tables receives the new object; free it with
+ * sqd_free_tables.  n_alpha * n_beta must be below 2^40 and each set below
+ * 2^31 strings.
+ * Errors: SQD_EINVAL (sizes, popcounts, unsorted sets, asymmetric integrals,
+ * non-finite integrals), SQD_ENOMEM.
+ */
+int sqd_excitation_tables(sqd_ctx *ctx, int norb,
+                          const uint64_t *d_alpha, int64_t n_alpha, int nalpha_e,
+                          const uint64_t *d_beta, int64_t n_beta, int nbeta_e,
+                          const double *d_h, const double *d_V, double ecore,
+                          sqd_tables **tables);
+
+void sqd_free_tables(sqd_tables *tables);
+
+/* Sizes of a table object.  info (host, 12 int64):
+ *  [0] norb, [1] n_alpha, [2] n_beta, [3] nnz singles alpha, [4] nnz doubles
+ *  alpha, [5] nnz singles beta, [6] nnz doubles beta, [7] shared (1 if one
+ *  table serves both spins), [8] device bytes held, [9] max singles per
+ *  string, [10] max doubles per string, [11] reserved. */
+int sqd_tables_info(const sqd_tables *tables, int64_t *info);
+
+/*
+ * Copy one excitation table to host buffers (for verification).
+ * spin: 0 alpha, 1 beta.  kind: 1 singles, 2 doubles.
+ * h_off (n+1 int64), h_tgt (nnz int32), h_orb (nnz*2 bytes p,q for kind 1;
+ * nnz*4 bytes i,j,a,b for kind 2), h_sign (nnz int8), h_val (nnz double).
+ * Any pointer may be NULL to skip that field.
+ */
+int sqd_tables_export(sqd_ctx *ctx, const sqd_tables *tables, int spin, int kind,
+                      int64_t *h_off, int32_t *h_tgt, uint8_t *h_orb,
+                      int8_t *h_sign, double *h_val);
+
+/*
+ * Diagonal H_II of every determinant into d_diag (device, n_alpha*n_beta):
+ * E_core + E_a(I_a) + E_b(I_b) + sum_{k in I_a, l in I_b} (kk|ll), the
+ * "diagonal terms" the Davidson time includes (Section VI).
+ */
+int sqd_diagonal(sqd_ctx *ctx, const sqd_tables *tables, double *d_diag);
+
+/* ------------------------------------------------- a5-a7: sigma = H C -- */
+
+/*
+ * sigma = (P H P) C for nvec vectors (Section II: matrix-vector product
+ * recomputing H_IJ; Section IV: three kinds of bra/ket pairs -- one or two
+ * alpha excitations, one or two beta excitations, one alpha and one beta
+ * excitation).  d_C and d_sigma are [nvec][n_alpha][n_beta] doubles
+ * (device, distinct buffers).  Asynchronous on the context's stream.
+ * Scratch (two n_alpha*n_beta vectors) is held by the tables object.
+ */
+int sqd_sigma(sqd_ctx *ctx, sqd_tables *tables, const double *d_C,
+              double *d_sigma, int nvec);
+
+/* ---------------------------------------------------- a8: Davidson -- */
+
+typedef struct {
+    int nroots;          /* number of lowest eigenpairs (>= 1)                 */
+    int max_iter;        /* iteration limit (e.g. 200)                         */
+    int max_subspace;    /* basis size limit; 0 = max(8*nroots, 16)            */
+    double tol_energy;   /* |theta - theta_previous| per root                  */
+    double tol_residual; /* ||H x - theta x||_2 per root                       */
+    double precond_floor;/* clamp of |theta - H_II| (e.g. 1e-8)                */
+    int use_guess;       /* 1: d_C holds nroots initial vectors                */
+    int reserved;
+} sqd_options;
+
+/*
+ * Davidson for the nroots lowest eigenpairs (Section I, Davidson 1975;
+ * one sigma per new vector and iteration, diagonal preconditioner,
+ * Gram-Schmidt, Section VI) with every step on the device.
+ *
+ * Guess: unit vectors on the nroots smallest H_II (ties: lower index), or
+ * the nroots vectors in d_C if use_guess.  Correction t = r / (theta -
+ * H_II) with |denominator| clamped to precond_floor; classical Gram-Schmidt
+ * twice, a vector is dropped if its norm after that is below 1e-12; at the
+ * subspace limit the basis restarts from the 2*nroots lowest Ritz vectors;
+ * converged when every root has ||r|| <= tol_residual and
+ * |delta theta| <= tol_energy.  Rayleigh-Ritz uses a one-block Jacobi
+ * eigensolver in FP64.
+ *
+ * Outputs: h_energies[nroots] (host), d_C [nroots][n_alpha][n_beta] the
+ * Ritz vectors (device, normalised, largest-magnitude component positive),
+ * *h_iters (host, may be NULL), h_residuals[nroots] (host, may be NULL).
+ * Returns SQD_ENOTCONVERGED (with the last estimates written) when max_iter
+ * is reached, SQD_EBREAKDOWN if no new direction survives orthogonalisation
+ * before convergence.
+ */
+int sqd_davidson(sqd_ctx *ctx, sqd_tables *tables, const sqd_options *opt,
+                 double *h_energies, double *d_C, int *h_iters,
+                 double *h_residuals);
+
+/* ------------------------------------------------ adjoint: RDMs ----- */
+
+/*
+ * Spin-summed reduced density matrices of the normalised state d_C
+ * ([n_alpha][n_beta], device): d_rdm1[p*norb+q] = sum_s <a+_{ps} a_{qs}>
+ * and, unless d_rdm2 is NULL, d_rdm2[((p*norb+q)*norb+r)*norb+s] =
+ * sum_{s,t} <a+_{ps} a+_{rt} a_{st} a_{qs}> (device outputs).  With C an
+ * eigenvector of P H P these are dE/dh_pq and 2 dE/d(pq|rs) element-wise
+ * (Hellmann-Feynman); E = E_core + sum h.rdm1 + 1/2 sum V.rdm2.
+ * Not in the paper: the adjoint of the subspace energy.
+ */
+int sqd_rdm(sqd_ctx *ctx, sqd_tables *tables, const double *d_C,
+            double *d_rdm1, double *d_rdm2);
+
+/* ------------------------------------------------------ measurement --- */
+
+/*
+ * Measurement counters (not in the paper; used to report throughput
+ * against the roofline).  sqd_profile_enable(ctx, 1) resets the counters
+ * and brackets every later kernel region of the library with CUDA events
+ * on the context stream; 0 resets and stops timing.
+ * Regions are booked in classes:
+ *   0 same_spin_alpha, 1 same_spin_beta, 2 alpha_beta, 3 transpose,
+ *   4 tables, 5 strings, 6 davidson, 7 rdm.
+ * sqd_profile_read returns, for one class, the class name (static string),
+ * the number of regions, their summed event time in ms, and the
+ * algorithmic FP64 flops and compulsory bytes booked for them (host
+ * outputs, each may be NULL).  It synchronises the stream.
+ * sqd_launch_count returns the number of kernels launched on the context
+ * since the last sqd_profile_enable call (counted with or without timing).
+ */
+int sqd_profile_enable(sqd_ctx *ctx, int enable);
+int sqd_profile_read(sqd_ctx *ctx, int cls, const char **name, int64_t *regions,
+                     double *ms, double *flops, double *bytes);
+int sqd_launch_count(const sqd_ctx *ctx, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SQD_H */

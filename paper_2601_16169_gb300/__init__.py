@@ -1,0 +1,321 @@
+"""Python binding of libsqd (include/sqd.h): the GB300 (sm_103a) hot path of
+sample-based quantum diagonalisation, arXiv 2601.16169.
+
+Argument marshalling only.  Every step -- string filtering, excitation
+tables, sigma = H C, the Davidson iteration, the RDMs -- runs in the CUDA
+kernels of ``libsqd.so``; PyTorch supplies device memory and the stream.
+There is no CPU fallback: without a built library or a CUDA device every
+call raises.
+
+The functions carry the C names without the ``sqd_`` prefix:
+``build_strings``, ``excitation_tables``, ``sigma``, ``davidson``, ``rdm``
+(plus ``diagonal`` and the ``Tables`` object's ``info``/``export``).
+Strings travel as ``torch.int64`` tensors holding the uint64 bit patterns.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import torch
+
+__all__ = [
+    "SQDError", "lib", "library_path", "Context", "Tables", "Options",
+    "build_strings", "excitation_tables", "sigma", "davidson", "diagonal", "rdm",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libsqd.so")
+_LIB = None
+
+SQD_OK = 0
+SQD_EINVAL = -1
+SQD_ENOMEM = -2
+SQD_ECUDA = -3
+SQD_ENOTCONVERGED = -4
+SQD_EBREAKDOWN = -5
+_NAMES = {0: "SQD_OK", -1: "SQD_EINVAL", -2: "SQD_ENOMEM", -3: "SQD_ECUDA",
+          -4: "SQD_ENOTCONVERGED", -5: "SQD_EBREAKDOWN", -6: "SQD_ETIMEOUT"}
+
+EXPORTED = [
+    "sqd_create", "sqd_set_stream", "sqd_destroy", "sqd_last_error", "sqd_version",
+    "sqd_build_strings", "sqd_excitation_tables", "sqd_free_tables", "sqd_tables_info",
+    "sqd_tables_export", "sqd_diagonal", "sqd_sigma", "sqd_davidson", "sqd_rdm",
+    "sqd_profile_enable", "sqd_profile_read", "sqd_launch_count",
+]
+
+PROFILE_CLASSES = ["same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose", "tables",
+                   "strings", "davidson", "rdm"]
+
+
+class SQDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_NAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    """sqd_options (see include/sqd.h)."""
+    _fields_ = [("nroots", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("max_subspace", ctypes.c_int), ("tol_energy", ctypes.c_double),
+                ("tol_residual", ctypes.c_double), ("precond_floor", ctypes.c_double),
+                ("use_guess", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libsqd.so.  Raises if it has not been built (no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(
+            "libsqd.so is not built (%s); run `python -c 'import __graft_entry__ as g; "
+            "g.build()'` or `python paper_2601_16169_gb300/build.py`" % _LIB_PATH)
+    L = ctypes.CDLL(_LIB_PATH)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    L.sqd_create.argtypes = [ctypes.POINTER(vp), i32, vp]
+    L.sqd_set_stream.argtypes = [vp, vp]
+    L.sqd_destroy.argtypes = [vp]
+    L.sqd_destroy.restype = None
+    L.sqd_last_error.argtypes = [vp]
+    L.sqd_last_error.restype = ctypes.c_char_p
+    L.sqd_version.restype = ctypes.c_char_p
+    L.sqd_build_strings.argtypes = [vp, vp, i64, i32, i32, vp, ctypes.POINTER(i64)]
+    L.sqd_excitation_tables.argtypes = [vp, i32, vp, i64, i32, vp, i64, i32, vp, vp, dbl,
+                                        ctypes.POINTER(vp)]
+    L.sqd_free_tables.argtypes = [vp]
+    L.sqd_free_tables.restype = None
+    L.sqd_tables_info.argtypes = [vp, vp]
+    L.sqd_tables_export.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp]
+    L.sqd_diagonal.argtypes = [vp, vp, vp]
+    L.sqd_sigma.argtypes = [vp, vp, vp, vp, i32]
+    L.sqd_davidson.argtypes = [vp, vp, ctypes.POINTER(Options), vp, vp,
+                               ctypes.POINTER(i32), vp]
+    L.sqd_rdm.argtypes = [vp, vp, vp, vp, vp]
+    L.sqd_profile_enable.argtypes = [vp, i32]
+    L.sqd_profile_read.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_char_p),
+                                   ctypes.POINTER(i64), ctypes.POINTER(dbl),
+                                   ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+    L.sqd_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
+    _LIB = L
+    return L
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _need_cuda(t: torch.Tensor, name: str, dtype):
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must have dtype %s" % (name, dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+
+
+class Context:
+    """An sqd_ctx bound to one device and (by default) torch's current stream."""
+
+    def __init__(self, device: Optional[int] = None, stream: Optional[torch.cuda.Stream] = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the SQD library has no CPU path")
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self._lib = lib()
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._stream = st
+        h = ctypes.c_void_p()
+        rc = self._lib.sqd_create(ctypes.byref(h), self.device, ctypes.c_void_p(st.cuda_stream))
+        if rc != SQD_OK:
+            raise SQDError(rc, self._lib.sqd_last_error(None).decode())
+        self.handle = h
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        self._stream = stream
+        self._check(self._lib.sqd_set_stream(self.handle, ctypes.c_void_p(stream.cuda_stream)))
+
+    @property
+    def stream(self):
+        return self._stream
+
+    def _check(self, rc, allow=()):
+        if rc != SQD_OK and rc not in allow:
+            raise SQDError(rc, self._lib.sqd_last_error(self.handle).decode())
+        return rc
+
+    def profile(self, enable: bool = True):
+        """sqd_profile_enable: reset the counters; time kernel regions if enable."""
+        self._check(self._lib.sqd_profile_enable(self.handle, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """sqd_profile_read for every class: {name: dict(regions, ms, flops, bytes)}."""
+        out = {}
+        for c in range(len(PROFILE_CLASSES)):
+            nm = ctypes.c_char_p()
+            reg = ctypes.c_int64()
+            ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+            self._check(self._lib.sqd_profile_read(self.handle, c, ctypes.byref(nm),
+                                                   ctypes.byref(reg), ctypes.byref(ms),
+                                                   ctypes.byref(fl), ctypes.byref(by)))
+            out[nm.value.decode()] = dict(regions=reg.value, ms=ms.value, flops=fl.value,
+                                          bytes=by.value)
+        return out
+
+    def launch_count(self) -> int:
+        """sqd_launch_count: kernels launched since the last profile() call."""
+        n = ctypes.c_int64()
+        self._check(self._lib.sqd_launch_count(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.sqd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Tables:
+    """Owner of an sqd_tables object (excitation lists, diagonal, scratch)."""
+
+    def __init__(self, ctx: Context, handle, norb: int, na: int, nb: int):
+        self.ctx, self.handle, self.norb, self.na, self.nb = ctx, handle, norb, na, nb
+
+    @property
+    def ndet(self) -> int:
+        return self.na * self.nb
+
+    def info(self) -> dict:
+        buf = (ctypes.c_int64 * 12)()
+        self.ctx._check(self.ctx._lib.sqd_tables_info(self.handle, buf))
+        keys = ["norb", "n_alpha", "n_beta", "nnz1_alpha", "nnz2_alpha", "nnz1_beta",
+                "nnz2_beta", "shared", "device_bytes", "max_singles", "max_doubles"]
+        return {k: int(buf[i]) for i, k in enumerate(keys)}
+
+    def export(self, spin: int, kind: int) -> dict:
+        """Host (numpy) copy of one excitation table: off, tgt, orb, sign, val."""
+        import numpy as np
+        n = self.na if spin == 0 else self.nb
+        inf = self.info()
+        nnz = inf[("nnz%d_%s" % (kind, "alpha" if spin == 0 else "beta"))]
+        off = np.zeros(n + 1, dtype=np.int64)
+        tgt = np.zeros(max(nnz, 1), dtype=np.int32)
+        orb = np.zeros((max(nnz, 1), 2 * kind), dtype=np.uint8)
+        sign = np.zeros(max(nnz, 1), dtype=np.int8)
+        val = np.zeros(max(nnz, 1), dtype=np.float64)
+        c = ctypes.c_void_p
+        self.ctx._check(self.ctx._lib.sqd_tables_export(
+            self.ctx.handle, self.handle, spin, kind, c(off.ctypes.data), c(tgt.ctypes.data),
+            c(orb.ctypes.data), c(sign.ctypes.data), c(val.ctypes.data)))
+        return dict(off=off, tgt=tgt[:nnz], orb=orb[:nnz], sign=sign[:nnz], val=val[:nnz])
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.ctx._lib.sqd_free_tables(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_strings(ctx: Context, raw: torch.Tensor, norb: int, nelec: int) -> torch.Tensor:
+    """sqd_build_strings: filter raw samples into the sorted set of distinct
+    strings with ``nelec`` electrons in ``norb`` orbitals."""
+    _need_cuda(raw, "raw", torch.int64)
+    out = torch.empty_like(raw)
+    n = ctypes.c_int64(0)
+    ctx._check(ctx._lib.sqd_build_strings(ctx.handle, _ptr(raw), raw.numel(), norb, nelec,
+                                          _ptr(out), ctypes.byref(n)))
+    return out[:n.value]
+
+
+def excitation_tables(ctx: Context, norb: int, alpha: torch.Tensor, nalpha_e: int,
+                      beta: torch.Tensor, nbeta_e: int, h: torch.Tensor, V: torch.Tensor,
+                      ecore: float = 0.0) -> Tables:
+    """sqd_excitation_tables.  Pass the same tensor for alpha and beta to
+    share one table between the spins."""
+    _need_cuda(alpha, "alpha", torch.int64)
+    _need_cuda(beta, "beta", torch.int64)
+    _need_cuda(h, "h", torch.float64)
+    _need_cuda(V, "V", torch.float64)
+    if h.numel() != norb * norb or V.numel() != norb ** 4:
+        raise ValueError("h must have norb^2 and V norb^4 elements")
+    t = ctypes.c_void_p()
+    ctx._check(ctx._lib.sqd_excitation_tables(
+        ctx.handle, norb, _ptr(alpha), alpha.numel(), nalpha_e,
+        _ptr(beta), beta.numel(), nbeta_e, _ptr(h), _ptr(V), float(ecore), ctypes.byref(t)))
+    return Tables(ctx, t, norb, alpha.numel(), beta.numel())
+
+
+def diagonal(ctx: Context, tables: Tables) -> torch.Tensor:
+    """sqd_diagonal: H_II of every determinant, shape (n_alpha, n_beta)."""
+    out = torch.empty((tables.na, tables.nb), dtype=torch.float64,
+                      device="cuda:%d" % ctx.device)
+    ctx._check(ctx._lib.sqd_diagonal(ctx.handle, tables.handle, _ptr(out)))
+    return out
+
+
+def sigma(ctx: Context, tables: Tables, C: torch.Tensor,
+          out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """sqd_sigma: sigma = H C.  C has shape (n_alpha, n_beta) or
+    (nvec, n_alpha, n_beta), float64, contiguous, on the device."""
+    _need_cuda(C, "C", torch.float64)
+    if C.numel() % tables.ndet != 0 or C.numel() == 0:
+        raise ValueError("C size is not a multiple of n_alpha * n_beta")
+    nvec = C.numel() // tables.ndet
+    if out is None:
+        out = torch.empty_like(C)
+    _need_cuda(out, "out", torch.float64)
+    ctx._check(ctx._lib.sqd_sigma(ctx.handle, tables.handle, _ptr(C), _ptr(out), nvec))
+    return out
+
+
+def davidson(ctx: Context, tables: Tables, nroots: int = 1, tol_residual: float = 1e-8,
+             tol_energy: float = 1e-8, max_iter: int = 200, max_subspace: int = 0,
+             precond_floor: float = 1e-8, guess: Optional[torch.Tensor] = None,
+             raise_on_nonconvergence: bool = True):
+    """sqd_davidson.  Returns (energies (numpy), C (nroots, n_alpha, n_beta)
+    tensor, iterations, residual norms (numpy), status code)."""
+    import numpy as np
+    C = torch.zeros((nroots, tables.na, tables.nb), dtype=torch.float64,
+                    device="cuda:%d" % ctx.device)
+    use_guess = 0
+    if guess is not None:
+        C.copy_(guess.reshape(C.shape))
+        use_guess = 1
+    o = Options(nroots=nroots, max_iter=max_iter, max_subspace=max_subspace,
+                tol_energy=tol_energy, tol_residual=tol_residual, precond_floor=precond_floor,
+                use_guess=use_guess, reserved=0)
+    e = np.zeros(nroots)
+    r = np.zeros(nroots)
+    it = ctypes.c_int(0)
+    allow = () if raise_on_nonconvergence else (SQD_ENOTCONVERGED, SQD_EBREAKDOWN)
+    rc = ctx._check(ctx._lib.sqd_davidson(ctx.handle, tables.handle, ctypes.byref(o),
+                                          ctypes.c_void_p(e.ctypes.data), _ptr(C),
+                                          ctypes.byref(it), ctypes.c_void_p(r.ctypes.data)),
+                    allow=allow)
+    return e, C, it.value, r, rc
+
+
+def rdm(ctx: Context, tables: Tables, C: torch.Tensor, two_body: bool = True):
+    """sqd_rdm: spin-summed 1-RDM (norb, norb) and 2-RDM (norb,)*4 of C."""
+    _need_cuda(C, "C", torch.float64)
+    n = tables.norb
+    dev = "cuda:%d" % ctx.device
+    g1 = torch.empty((n, n), dtype=torch.float64, device=dev)
+    g2 = torch.empty((n, n, n, n), dtype=torch.float64, device=dev) if two_body else None
+    ctx._check(ctx._lib.sqd_rdm(ctx.handle, tables.handle, _ptr(C), _ptr(g1), _ptr(g2)))
+    return g1, g2

@@ -1,0 +1,739 @@
+// C ABI of the SQD library (include/sqd.h): context, validation, string
+// filtering, table construction, sigma, Davidson and RDM orchestration.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "sqd_internal.cuh"
+
+int build_ab_schedule(sqd_ctx *ctx, sqd_tables *t);
+
+static thread_local std::string g_err;
+
+static int fail_noctx(int code, const char *msg) {
+    g_err = msg;
+    return code;
+}
+
+template <typename T>
+static int dalloc(sqd_ctx *ctx, T **p, int64_t count, int64_t *bytes = nullptr) {
+    size_t b = sizeof(T) * (size_t)(count > 0 ? count : 1);
+    cudaError_t e = cudaMalloc((void **)p, b);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return sqd_fail(ctx, e == cudaErrorMemoryAllocation ? SQD_ENOMEM : SQD_ECUDA,
+                        "cudaMalloc(%zu) failed: %s", b, cudaGetErrorString(e));
+    }
+    if (bytes) *bytes += (int64_t)b;
+    return SQD_OK;
+}
+
+static int64_t next_pow2(int64_t x) {
+    int64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// ---------------------------------------------------------- profiling ----
+
+static cudaEvent_t pool_event(sqd_ctx *ctx) {
+    if (!ctx->pool.empty()) {
+        cudaEvent_t e = ctx->pool.back();
+        ctx->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(sqd_ctx *ctx, int cls) {
+    if (!ctx->prof) return;
+    if (ctx->open_cls >= 0) {  // a region left open by an error return: drop it
+        ctx->pool.push_back(ctx->recs.back().a);
+        ctx->pool.push_back(ctx->recs.back().b);
+        ctx->recs.pop_back();
+        ctx->open_cls = -1;
+    }
+    prof_rec r;
+    r.cls = cls;
+    r.a = pool_event(ctx);
+    r.b = pool_event(ctx);
+    cudaEventRecord(r.a, ctx->stream);
+    ctx->recs.push_back(r);
+    ctx->open_cls = cls;
+}
+
+void prof_end(sqd_ctx *ctx, double flops, double bytes) {
+    if (!ctx->prof || ctx->open_cls < 0) return;
+    prof_rec &r = ctx->recs.back();
+    cudaEventRecord(r.b, ctx->stream);
+    ctx->cls_launches[r.cls]++;
+    ctx->cls_flops[r.cls] += flops;
+    ctx->cls_bytes[r.cls] += bytes;
+    ctx->open_cls = -1;
+}
+
+// fold finished event pairs into the per-class times
+static int prof_collect(sqd_ctx *ctx) {
+    if (ctx->recs.empty()) return SQD_OK;
+    if (ctx->open_cls >= 0) {
+        ctx->pool.push_back(ctx->recs.back().a);
+        ctx->pool.push_back(ctx->recs.back().b);
+        ctx->recs.pop_back();
+        ctx->open_cls = -1;
+    }
+    SQD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (prof_rec &r : ctx->recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) ctx->cls_ms[r.cls] += ms;
+        else cudaGetLastError();
+        ctx->pool.push_back(r.a);
+        ctx->pool.push_back(r.b);
+    }
+    ctx->recs.clear();
+    return SQD_OK;
+}
+
+static int use_device(sqd_ctx *ctx) {
+    SQD_CUDA(ctx, cudaSetDevice(ctx->device));
+    return SQD_OK;
+}
+
+extern "C" {
+
+const char *sqd_version(void) { return "sqd-gb300 0.1"; }
+
+int sqd_create(sqd_ctx **out, int device, void *stream) {
+    if (!out) return fail_noctx(SQD_EINVAL, "sqd_create: out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0)
+        return fail_noctx(SQD_ECUDA, "sqd_create: no CUDA device available");
+    if (device < 0 || device >= ndev) return fail_noctx(SQD_EINVAL, "sqd_create: bad device");
+    sqd_ctx *ctx = new sqd_ctx();
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)stream;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) !=
+            cudaSuccess) {
+        delete ctx;
+        return fail_noctx(SQD_ECUDA, "sqd_create: cannot use device");
+    }
+    *out = ctx;
+    return SQD_OK;
+}
+
+int sqd_set_stream(sqd_ctx *ctx, void *stream) {
+    if (!ctx) return fail_noctx(SQD_EINVAL, "sqd_set_stream: ctx is NULL");
+    ctx->stream = (cudaStream_t)stream;
+    return SQD_OK;
+}
+
+void sqd_destroy(sqd_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (!ctx->recs.empty()) cudaStreamSynchronize(ctx->stream);
+    for (prof_rec &r : ctx->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+    delete ctx;
+}
+
+static const char *k_prof_names[PROF_NCLASS] = {
+    "same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose",
+    "tables",          "strings",        "davidson",   "rdm"};
+
+int sqd_profile_enable(sqd_ctx *ctx, int enable) {
+    if (!ctx) return fail_noctx(SQD_EINVAL, "sqd_profile_enable: ctx is NULL");
+    SQD_TRY(use_device(ctx));
+    SQD_TRY(prof_collect(ctx));
+    for (int c = 0; c < PROF_NCLASS; c++) {
+        ctx->cls_launches[c] = 0;
+        ctx->cls_flops[c] = ctx->cls_bytes[c] = ctx->cls_ms[c] = 0.0;
+    }
+    ctx->launches = 0;
+    ctx->prof = enable != 0;
+    return SQD_OK;
+}
+
+int sqd_profile_read(sqd_ctx *ctx, int cls, const char **name, int64_t *regions, double *ms,
+                     double *flops, double *bytes) {
+    if (!ctx) return fail_noctx(SQD_EINVAL, "sqd_profile_read: ctx is NULL");
+    if (cls < 0 || cls >= PROF_NCLASS) return sqd_fail(ctx, SQD_EINVAL, "bad profile class");
+    SQD_TRY(use_device(ctx));
+    SQD_TRY(prof_collect(ctx));
+    if (name) *name = k_prof_names[cls];
+    if (regions) *regions = ctx->cls_launches[cls];
+    if (ms) *ms = ctx->cls_ms[cls];
+    if (flops) *flops = ctx->cls_flops[cls];
+    if (bytes) *bytes = ctx->cls_bytes[cls];
+    return SQD_OK;
+}
+
+int sqd_launch_count(const sqd_ctx *ctx, int64_t *launches) {
+    if (!ctx || !launches) return fail_noctx(SQD_EINVAL, "sqd_launch_count: NULL argument");
+    *launches = ctx->launches;
+    return SQD_OK;
+}
+
+const char *sqd_last_error(const sqd_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_err.c_str();
+}
+
+// --------------------------------------------------------- a1: strings --
+
+int sqd_build_strings(sqd_ctx *ctx, const uint64_t *d_raw, int64_t n_raw, int norb, int nelec,
+                      uint64_t *d_out, int64_t *n_out) {
+    if (!ctx) return fail_noctx(SQD_EINVAL, "sqd_build_strings: ctx is NULL");
+    if (!n_out) return sqd_fail(ctx, SQD_EINVAL, "sqd_build_strings: n_out is NULL");
+    *n_out = 0;
+    if (norb < 1 || norb > 64) return sqd_fail(ctx, SQD_EINVAL, "norb must be in [1, 64]");
+    if (nelec < 0 || nelec > norb) return sqd_fail(ctx, SQD_EINVAL, "nelec must be in [0, norb]");
+    if (n_raw < 0) return sqd_fail(ctx, SQD_EINVAL, "n_raw < 0");
+    if (n_raw == 0) return SQD_OK;
+    if (!d_raw || !d_out) return sqd_fail(ctx, SQD_EINVAL, "NULL string buffer");
+    SQD_TRY(use_device(ctx));
+    prof_begin(ctx, PROF_STRINGS);
+    cudaStream_t st = ctx->stream;
+    int64_t *flags = nullptr, *pos = nullptr, *tot = nullptr;
+    uint64_t *keys = nullptr;
+    SQD_CUDA(ctx, cudaMallocAsync((void **)&flags, sizeof(int64_t) * n_raw, st));
+    SQD_CUDA(ctx, cudaMallocAsync((void **)&pos, sizeof(int64_t) * n_raw, st));
+    SQD_CUDA(ctx, cudaMallocAsync((void **)&tot, sizeof(int64_t), st));
+    SQD_TRY(launch_filter_flags(ctx, d_raw, n_raw, norb, nelec, flags));
+    SQD_TRY(launch_exclusive_scan(ctx, flags, pos, n_raw, tot));
+    int64_t m = 0;
+    SQD_CUDA(ctx, cudaMemcpyAsync(&m, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SQD_CUDA(ctx, cudaStreamSynchronize(st));
+    int64_t P = next_pow2(m > 0 ? m : 1);
+    SQD_CUDA(ctx, cudaMallocAsync((void **)&keys, sizeof(uint64_t) * P, st));
+    SQD_TRY(launch_fill_u64(ctx, keys, P, ~0ull));
+    SQD_TRY(launch_scatter_flagged(ctx, d_raw, flags, pos, n_raw, keys));
+    SQD_TRY(launch_bitonic_sort_u64(ctx, keys, P));
+    // keys[0..m) sorted; mark first occurrences and compact into d_out
+    SQD_TRY(launch_unique_flags(ctx, keys, m, flags));
+    SQD_TRY(launch_exclusive_scan(ctx, flags, pos, m, tot));
+    SQD_TRY(launch_scatter_flagged(ctx, keys, flags, pos, m, d_out));
+    int64_t u = 0;
+    SQD_CUDA(ctx, cudaMemcpyAsync(&u, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SQD_CUDA(ctx, cudaFreeAsync(flags, st));
+    SQD_CUDA(ctx, cudaFreeAsync(pos, st));
+    SQD_CUDA(ctx, cudaFreeAsync(tot, st));
+    SQD_CUDA(ctx, cudaFreeAsync(keys, st));
+    prof_end(ctx, 0.0, 8.0 * n_raw);
+    SQD_CUDA(ctx, cudaStreamSynchronize(st));
+    *n_out = m > 0 ? u : 0;
+    return SQD_OK;
+}
+
+// ----------------------------------------------------------- a2-a4 ------
+
+static void free_spin(spin_tables *s) {
+    void *ptrs[] = {s->str,  s->off1, s->tgt1, s->pq1,  s->sgn1,   s->val1, s->off2,
+                    s->tgt2, s->orb2, s->sgn2, s->val2, s->energy, s->W,    s->u};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    *s = spin_tables();
+}
+
+static int build_kind(sqd_ctx *ctx, sqd_tables *t, spin_tables *s, int kind) {
+    cudaStream_t st = ctx->stream;
+    const int64_t n = s->n;
+    int64_t *counts = nullptr, *cursor = nullptr, *tot = nullptr, *off = nullptr;
+    SQD_CUDA(ctx, cudaMallocAsync((void **)&counts, sizeof(int64_t) * n, st));
+    SQD_CUDA(ctx, cudaMallocAsync((void **)&cursor, sizeof(int64_t) * n, st));
+    SQD_CUDA(ctx, cudaMallocAsync((void **)&tot, sizeof(int64_t), st));
+    SQD_TRY(dalloc(ctx, &off, n + 1, &t->bytes));
+    SQD_TRY(launch_count_excitations(ctx, s->str, n, t->norb, kind, counts));
+    SQD_TRY(launch_exclusive_scan(ctx, counts, off, n, off + n));
+    int64_t nnz = 0;
+    SQD_CUDA(ctx, cudaMemcpyAsync(&nnz, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SQD_CUDA(ctx, cudaStreamSynchronize(st));
+    int64_t P = next_pow2(nnz > 0 ? nnz : 1);
+    uint64_t *keys = nullptr;
+    SQD_CUDA(ctx, cudaMallocAsync((void **)&keys, sizeof(uint64_t) * P, st));
+    SQD_TRY(launch_fill_u64(ctx, keys, P, ~0ull));
+    SQD_TRY(launch_fill_excitations(ctx, s->str, n, t->norb, kind, off, cursor, keys));
+    SQD_TRY(launch_bitonic_sort_u64(ctx, keys, P));
+    std::vector<int64_t> hoff(n + 1);
+    SQD_CUDA(ctx, cudaMemcpyAsync(hoff.data(), off, sizeof(int64_t) * (n + 1),
+                                  cudaMemcpyDeviceToHost, st));
+    if (kind == 1) {
+        s->nnz1 = nnz;
+        s->off1 = off;
+        SQD_TRY(dalloc(ctx, &s->tgt1, nnz, &t->bytes));
+        SQD_TRY(dalloc(ctx, &s->pq1, nnz, &t->bytes));
+        SQD_TRY(dalloc(ctx, &s->sgn1, nnz, &t->bytes));
+        SQD_TRY(dalloc(ctx, &s->val1, nnz, &t->bytes));
+        SQD_TRY(launch_finalize_singles(ctx, s->str, t->norb, keys, nnz, t->h, t->V, s->tgt1,
+                                        s->pq1, s->sgn1, s->val1));
+    } else {
+        s->nnz2 = nnz;
+        s->off2 = off;
+        SQD_TRY(dalloc(ctx, &s->tgt2, nnz, &t->bytes));
+        SQD_TRY(dalloc(ctx, &s->orb2, nnz, &t->bytes));
+        SQD_TRY(dalloc(ctx, &s->sgn2, nnz, &t->bytes));
+        SQD_TRY(dalloc(ctx, &s->val2, nnz, &t->bytes));
+        SQD_TRY(launch_finalize_doubles(ctx, s->str, t->norb, keys, nnz, t->V, s->tgt2, s->orb2,
+                                        s->sgn2, s->val2));
+    }
+    SQD_CUDA(ctx, cudaFreeAsync(keys, st));
+    SQD_CUDA(ctx, cudaFreeAsync(counts, st));
+    SQD_CUDA(ctx, cudaFreeAsync(cursor, st));
+    SQD_CUDA(ctx, cudaFreeAsync(tot, st));
+    SQD_CUDA(ctx, cudaStreamSynchronize(st));
+    int64_t mx = 0;
+    for (int64_t i = 0; i < n; i++) mx = std::max(mx, hoff[i + 1] - hoff[i]);
+    if (kind == 1) {
+        s->max1 = mx;
+        s->h_off1 = std::move(hoff);
+    } else {
+        s->max2 = mx;
+    }
+    return SQD_OK;
+}
+
+static int build_spin(sqd_ctx *ctx, sqd_tables *t, spin_tables *s, const uint64_t *d_str,
+                      int64_t n, int ne) {
+    s->n = n;
+    s->ne = ne;
+    SQD_TRY(dalloc(ctx, &s->str, n, &t->bytes));
+    SQD_CUDA(ctx, cudaMemcpyAsync(s->str, d_str, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+    SQD_TRY(build_kind(ctx, t, s, 1));
+    SQD_TRY(build_kind(ctx, t, s, 2));
+    const int64_t n2 = (int64_t)t->norb * t->norb;
+    SQD_TRY(dalloc(ctx, &s->energy, n, &t->bytes));
+    SQD_TRY(dalloc(ctx, &s->W, n2 * n, &t->bytes));
+    SQD_TRY(launch_string_terms(ctx, s->str, n, t->norb, t->h, t->V, s->energy, s->W, nullptr));
+    return SQD_OK;
+}
+
+static int check_set(sqd_ctx *ctx, const uint64_t *d, int64_t n, int norb, int ne,
+                     const char *name) {
+    int *bad = nullptr;
+    SQD_CUDA(ctx, cudaMallocAsync((void **)&bad, sizeof(int), ctx->stream));
+    SQD_CUDA(ctx, cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream));
+    SQD_TRY(launch_check_sorted_unique(ctx, d, n, norb, ne, bad));
+    int hb = 0;
+    SQD_CUDA(ctx, cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    SQD_CUDA(ctx, cudaFreeAsync(bad, ctx->stream));
+    SQD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (hb & 1) return sqd_fail(ctx, SQD_EINVAL, "%s strings: wrong electron count", name);
+    if (hb & 2) return sqd_fail(ctx, SQD_EINVAL, "%s strings: orbital index >= norb", name);
+    if (hb & 4) return sqd_fail(ctx, SQD_EINVAL, "%s strings: not sorted ascending/unique", name);
+    return SQD_OK;
+}
+
+static int tables_impl(sqd_ctx *ctx, sqd_tables *t, int norb, const uint64_t *d_alpha,
+                       int64_t n_alpha, int nalpha_e, const uint64_t *d_beta, int64_t n_beta,
+                       int nbeta_e, const double *d_h, const double *d_V, double ecore) {
+    const int64_t n2 = (int64_t)norb * norb, n4 = n2 * n2;
+    SQD_TRY(check_set(ctx, d_alpha, n_alpha, norb, nalpha_e, "alpha"));
+    SQD_TRY(check_set(ctx, d_beta, n_beta, norb, nbeta_e, "beta"));
+    double *res = nullptr;
+    SQD_CUDA(ctx, cudaMallocAsync((void **)&res, sizeof(double) * 3, ctx->stream));
+    SQD_CUDA(ctx, cudaMemsetAsync(res, 0, sizeof(double) * 3, ctx->stream));
+    SQD_TRY(launch_check_integrals(ctx, d_h, d_V, norb, res));
+    double hres[3];
+    SQD_CUDA(ctx, cudaMemcpyAsync(hres, res, sizeof(hres), cudaMemcpyDeviceToHost, ctx->stream));
+    SQD_CUDA(ctx, cudaFreeAsync(res, ctx->stream));
+    SQD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (hres[2] != 0.0) return sqd_fail(ctx, SQD_EINVAL, "integrals contain NaN or Inf");
+    if (hres[0] > 1e-10 * std::max(1.0, hres[1]))
+        return sqd_fail(ctx, SQD_EINVAL,
+                        "integrals are not symmetric (max deviation %.3e): h must be symmetric "
+                        "and V 8-fold symmetric",
+                        hres[0]);
+    t->norb = norb;
+    t->ecore = ecore;
+    SQD_TRY(dalloc(ctx, &t->h, n2, &t->bytes));
+    SQD_TRY(dalloc(ctx, &t->V, n4, &t->bytes));
+    SQD_CUDA(ctx, cudaMemcpyAsync(t->h, d_h, sizeof(double) * n2, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+    SQD_CUDA(ctx, cudaMemcpyAsync(t->V, d_V, sizeof(double) * n4, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+    SQD_TRY(build_spin(ctx, t, &t->a, d_alpha, n_alpha, nalpha_e));
+    t->shared = (d_alpha == d_beta && n_alpha == n_beta && nalpha_e == nbeta_e);
+    if (t->shared) {
+        t->b = &t->a;
+    } else {
+        SQD_TRY(build_spin(ctx, t, &t->b_own, d_beta, n_beta, nbeta_e));
+        t->b = &t->b_own;
+    }
+    SQD_TRY(dalloc(ctx, &t->diag, n_alpha * n_beta, &t->bytes));
+    SQD_TRY(launch_diagonal(ctx, &t->a, t->b, norb, ecore, t->a.str, t->diag));
+    SQD_TRY(build_ab_schedule(ctx, t));
+    SQD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return SQD_OK;
+}
+
+int sqd_excitation_tables(sqd_ctx *ctx, int norb, const uint64_t *d_alpha, int64_t n_alpha,
+                          int nalpha_e, const uint64_t *d_beta, int64_t n_beta, int nbeta_e,
+                          const double *d_h, const double *d_V, double ecore,
+                          sqd_tables **tables) {
+    if (!ctx) return fail_noctx(SQD_EINVAL, "sqd_excitation_tables: ctx is NULL");
+    if (!tables) return sqd_fail(ctx, SQD_EINVAL, "tables is NULL");
+    *tables = nullptr;
+    if (norb < 1 || norb > 64) return sqd_fail(ctx, SQD_EINVAL, "norb must be in [1, 64]");
+    if (nalpha_e < 0 || nalpha_e > norb || nbeta_e < 0 || nbeta_e > norb)
+        return sqd_fail(ctx, SQD_EINVAL, "electron count must be in [0, norb]");
+    if (n_alpha < 1 || n_beta < 1) return sqd_fail(ctx, SQD_EINVAL, "empty string set");
+    if (n_alpha >= (1LL << 31) || n_beta >= (1LL << 31))
+        return sqd_fail(ctx, SQD_EINVAL, "string set too large (>= 2^31)");
+    if ((double)n_alpha * (double)n_beta >= 1099511627776.0)
+        return sqd_fail(ctx, SQD_EINVAL, "subspace too large (>= 2^40 determinants)");
+    if (!d_alpha || !d_beta || !d_h || !d_V) return sqd_fail(ctx, SQD_EINVAL, "NULL input");
+    if (!std::isfinite(ecore)) return sqd_fail(ctx, SQD_EINVAL, "ecore is not finite");
+    SQD_TRY(use_device(ctx));
+    sqd_tables *t = new sqd_tables();
+    t->ctx = ctx;
+    prof_begin(ctx, PROF_TABLES);
+    int r = tables_impl(ctx, t, norb, d_alpha, n_alpha, nalpha_e, d_beta, n_beta, nbeta_e, d_h,
+                        d_V, ecore);
+    prof_end(ctx, 0.0, 0.0);
+    if (r != SQD_OK) {
+        cudaStreamSynchronize(ctx->stream);
+        sqd_free_tables(t);
+        return r;
+    }
+    *tables = t;
+    return SQD_OK;
+}
+
+void sqd_free_tables(sqd_tables *t) {
+    if (!t) return;
+    if (t->ctx) cudaSetDevice(t->ctx->device);
+    cudaDeviceSynchronize();
+    free_spin(&t->a);
+    if (!t->shared) free_spin(&t->b_own);
+    void *ptrs[] = {t->h, t->V, t->diag, t->ab.chunk_rows, t->ab.group_rows, t->scratch_t,
+                    t->scratch_s};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete t;
+}
+
+int sqd_tables_info(const sqd_tables *t, int64_t *info) {
+    if (!t || !info) return fail_noctx(SQD_EINVAL, "sqd_tables_info: NULL argument");
+    info[0] = t->norb;
+    info[1] = t->a.n;
+    info[2] = t->b->n;
+    info[3] = t->a.nnz1;
+    info[4] = t->a.nnz2;
+    info[5] = t->b->nnz1;
+    info[6] = t->b->nnz2;
+    info[7] = t->shared ? 1 : 0;
+    info[8] = t->bytes;
+    info[9] = std::max(t->a.max1, t->b->max1);
+    info[10] = std::max(t->a.max2, t->b->max2);
+    info[11] = 0;
+    return SQD_OK;
+}
+
+int sqd_tables_export(sqd_ctx *ctx, const sqd_tables *t, int spin, int kind, int64_t *h_off,
+                      int32_t *h_tgt, uint8_t *h_orb, int8_t *h_sign, double *h_val) {
+    if (!ctx || !t) return fail_noctx(SQD_EINVAL, "sqd_tables_export: NULL argument");
+    if ((spin != 0 && spin != 1) || (kind != 1 && kind != 2))
+        return sqd_fail(ctx, SQD_EINVAL, "spin must be 0/1 and kind 1/2");
+    SQD_TRY(use_device(ctx));
+    const spin_tables *s = spin ? t->b : &t->a;
+    int64_t n = s->n, nnz = kind == 1 ? s->nnz1 : s->nnz2;
+    cudaStream_t st = ctx->stream;
+    if (h_off)
+        SQD_CUDA(ctx, cudaMemcpyAsync(h_off, kind == 1 ? s->off1 : s->off2,
+                                      sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, st));
+    if (nnz > 0) {
+        if (h_tgt)
+            SQD_CUDA(ctx, cudaMemcpyAsync(h_tgt, kind == 1 ? s->tgt1 : s->tgt2,
+                                          sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, st));
+        if (h_sign)
+            SQD_CUDA(ctx, cudaMemcpyAsync(h_sign, kind == 1 ? s->sgn1 : s->sgn2, nnz,
+                                          cudaMemcpyDeviceToHost, st));
+        if (h_val)
+            SQD_CUDA(ctx, cudaMemcpyAsync(h_val, kind == 1 ? s->val1 : s->val2,
+                                          sizeof(double) * nnz, cudaMemcpyDeviceToHost, st));
+    }
+    std::vector<uint16_t> pq;
+    if (h_orb && nnz > 0) {
+        if (kind == 2) {
+            SQD_CUDA(ctx, cudaMemcpyAsync(h_orb, s->orb2, sizeof(uint32_t) * nnz,
+                                          cudaMemcpyDeviceToHost, st));
+        } else {
+            pq.resize(nnz);
+            SQD_CUDA(ctx, cudaMemcpyAsync(pq.data(), s->pq1, sizeof(uint16_t) * nnz,
+                                          cudaMemcpyDeviceToHost, st));
+        }
+    }
+    SQD_CUDA(ctx, cudaStreamSynchronize(st));
+    if (!pq.empty()) {
+        for (int64_t e = 0; e < nnz; e++) {
+            h_orb[2 * e] = (uint8_t)(pq[e] / t->norb);
+            h_orb[2 * e + 1] = (uint8_t)(pq[e] % t->norb);
+        }
+    }
+    return SQD_OK;
+}
+
+int sqd_diagonal(sqd_ctx *ctx, const sqd_tables *t, double *d_diag) {
+    if (!ctx || !t) return fail_noctx(SQD_EINVAL, "sqd_diagonal: NULL argument");
+    if (!d_diag) return sqd_fail(ctx, SQD_EINVAL, "d_diag is NULL");
+    SQD_TRY(use_device(ctx));
+    SQD_CUDA(ctx, cudaMemcpyAsync(d_diag, t->diag, sizeof(double) * t->a.n * t->b->n,
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+    return SQD_OK;
+}
+
+// ------------------------------------------------------------ a5-a7 -----
+
+static int ensure_scratch(sqd_ctx *ctx, sqd_tables *t) {
+    const int64_t N = t->a.n * t->b->n;
+    if (!t->scratch_t) SQD_TRY(dalloc(ctx, &t->scratch_t, N, &t->bytes));
+    if (!t->scratch_s) SQD_TRY(dalloc(ctx, &t->scratch_s, N, &t->bytes));
+    return SQD_OK;
+}
+
+// Algorithmic FP64 flops of the sigma terms (2 per multiply-add):
+//  alpha side: N (diagonal) + nb*(2*nnz1_a + nnz2_a)   [single: value + W coupling]
+//  beta side : na*(2*nnz1_b + nnz2_b)
+//  alpha-beta: nnz1_a * nnz1_b
+// and their compulsory HBM bytes (read C, read/write sigma, the diagonal).
+static void sigma_work(const sqd_tables *t, double *f_a, double *f_b, double *f_ab) {
+    const double na = (double)t->a.n, nb = (double)t->b->n;
+    *f_a = 2.0 * (na * nb + nb * (2.0 * t->a.nnz1 + t->a.nnz2));
+    *f_b = 2.0 * na * (2.0 * t->b->nnz1 + t->b->nnz2);
+    *f_ab = 2.0 * (double)t->a.nnz1 * (double)t->b->nnz1;
+}
+
+static int sigma_impl(sqd_ctx *ctx, sqd_tables *t, const double *C, double *S, int nvec) {
+    const int64_t na = t->a.n, nb = t->b->n, N = na * nb;
+    const double vb = 8.0 * (double)N;
+    double f_a, f_b, f_ab;
+    sigma_work(t, &f_a, &f_b, &f_ab);
+    SQD_TRY(ensure_scratch(ctx, t));
+    for (int v = 0; v < nvec; v++) {
+        const double *Cv = C + (int64_t)v * N;
+        double *Sv = S + (int64_t)v * N;
+        // alpha side (+ diagonal): writes sigma
+        prof_begin(ctx, PROF_SAME_ALPHA);
+        SQD_TRY(launch_same_spin(ctx, &t->a, t->b, na, nb, Cv, Sv, t->diag));
+        prof_end(ctx, f_a, 3 * vb);
+        // alpha-beta paired singles: adds into sigma
+        prof_begin(ctx, PROF_ALPHA_BETA);
+        SQD_TRY(launch_alpha_beta(ctx, t, Cv, Sv));
+        prof_end(ctx, f_ab, 3 * vb);
+        // beta side on C^T, added back transposed
+        prof_begin(ctx, PROF_TRANSPOSE);
+        SQD_TRY(launch_transpose(ctx, Cv, t->scratch_t, na, nb, false));
+        prof_end(ctx, 0.0, 2 * vb);
+        prof_begin(ctx, PROF_SAME_BETA);
+        SQD_TRY(launch_same_spin(ctx, t->b, &t->a, nb, na, t->scratch_t, t->scratch_s, nullptr));
+        prof_end(ctx, f_b, 2 * vb);
+        prof_begin(ctx, PROF_TRANSPOSE);
+        SQD_TRY(launch_transpose(ctx, t->scratch_s, Sv, nb, na, true));
+        prof_end(ctx, 0.0, 3 * vb);
+    }
+    return SQD_OK;
+}
+
+int sqd_sigma(sqd_ctx *ctx, sqd_tables *t, const double *d_C, double *d_sigma, int nvec) {
+    if (!ctx || !t) return fail_noctx(SQD_EINVAL, "sqd_sigma: NULL argument");
+    if (nvec < 1) return sqd_fail(ctx, SQD_EINVAL, "nvec must be >= 1");
+    if (!d_C || !d_sigma) return sqd_fail(ctx, SQD_EINVAL, "NULL vector");
+    if (d_C == d_sigma) return sqd_fail(ctx, SQD_EINVAL, "d_C and d_sigma must differ");
+    SQD_TRY(use_device(ctx));
+    return sigma_impl(ctx, t, d_C, d_sigma, nvec);
+}
+
+// --------------------------------------------------------- a8: Davidson --
+
+struct dav_work {
+    double *Vb = nullptr, *Wb = nullptr, *X = nullptr, *R = nullptr, *Tmp = nullptr;
+    double *G = nullptr, *evals = nullptr, *evecs = nullptr, *dots = nullptr, *partial = nullptr;
+    double *phase = nullptr;
+    int64_t *idx = nullptr;
+    ~dav_work() {
+        void *p[] = {Vb, Wb, X, R, Tmp, G, evals, evecs, dots, partial, phase, idx};
+        for (void *q : p)
+            if (q) cudaFree(q);
+    }
+};
+
+static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, double *h_energies,
+                         double *d_C, int *h_iters, double *h_res) {
+    cudaStream_t st = ctx->stream;
+    const int64_t N = t->a.n * t->b->n;
+    const int k = o->nroots;
+    int M = o->max_subspace > 0 ? o->max_subspace : std::max(8 * k, 16);
+    if (M > 112) M = 112;
+    if ((int64_t)M > N) M = (int)N;
+    if (M < std::min<int64_t>(3 * k, N))
+        return sqd_fail(ctx, SQD_EINVAL, "max_subspace must be >= 3*nroots (or the dimension)");
+    const int nblk = multidot_blocks(N);
+    const int k2 = std::min(2 * k, M);
+    dav_work w;
+    SQD_TRY(dalloc(ctx, &w.Vb, (int64_t)M * N));
+    SQD_TRY(dalloc(ctx, &w.Wb, (int64_t)M * N));
+    SQD_TRY(dalloc(ctx, &w.X, (int64_t)k * N));
+    SQD_TRY(dalloc(ctx, &w.R, (int64_t)k * N));
+    SQD_TRY(dalloc(ctx, &w.Tmp, (int64_t)k2 * N));
+    SQD_TRY(dalloc(ctx, &w.G, (int64_t)M * M));
+    SQD_TRY(dalloc(ctx, &w.evals, M));
+    SQD_TRY(dalloc(ctx, &w.evecs, (int64_t)M * M));
+    SQD_TRY(dalloc(ctx, &w.dots, M));
+    SQD_TRY(dalloc(ctx, &w.partial, (int64_t)M * nblk));
+    SQD_TRY(dalloc(ctx, &w.phase, 3 * 4 * ctx->sm_count + 8));
+    SQD_TRY(dalloc(ctx, &w.idx, k));
+    SQD_TRY(ensure_scratch(ctx, t));
+
+    auto dot_col = [&](int m, int64_t j) -> int {
+        // G[0..m, j] = Vb[0..m) . Wb_j  (upper triangle column j, m = j+1)
+        return launch_multidot(ctx, w.Vb, N, m, w.Wb + j * N, N, w.partial, nblk,
+                               w.G + j * M);
+    };
+    // CGS2 of Vb[m] against Vb[0..m); returns its norm^2 on the host
+    auto orthonormalize = [&](int m, double *nrm2) -> int {
+        double *v = w.Vb + (int64_t)m * N;
+        for (int pass = 0; pass < 2; pass++) {
+            if (m == 0) break;
+            SQD_TRY(launch_multidot(ctx, w.Vb, N, m, v, N, w.partial, nblk, w.dots));
+            SQD_TRY(launch_gemv_sub(ctx, w.Vb, N, m, w.dots, v, N));
+        }
+        SQD_TRY(launch_multidot(ctx, v, N, 1, v, N, w.partial, nblk, w.dots));
+        SQD_CUDA(ctx, cudaMemcpyAsync(nrm2, w.dots, sizeof(double), cudaMemcpyDeviceToHost, st));
+        SQD_CUDA(ctx, cudaStreamSynchronize(st));
+        return SQD_OK;
+    };
+
+    int m = 0;
+    if (o->use_guess) {
+        for (int j = 0; j < k; j++) {
+            SQD_CUDA(ctx, cudaMemcpyAsync(w.Vb + (int64_t)m * N, d_C + (int64_t)j * N,
+                                          sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+            double n2 = 0.0;
+            SQD_TRY(orthonormalize(m, &n2));
+            if (!(std::sqrt(n2) >= 1e-12)) continue;
+            SQD_TRY(launch_scale(ctx, w.Vb + (int64_t)m * N, N, w.dots, 1));
+            m++;
+        }
+        if (m < k) return sqd_fail(ctx, SQD_EINVAL, "initial guess vectors are linearly dependent");
+    } else {
+        SQD_CUDA(ctx, cudaMemsetAsync(w.Vb, 0, sizeof(double) * k * N, st));
+        SQD_TRY(launch_argmin_k(ctx, t->diag, N, k, w.idx));
+        SQD_TRY(launch_set_unit(ctx, w.Vb, N, k, w.idx));
+        m = k;
+    }
+    SQD_TRY(sigma_impl(ctx, t, w.Vb, w.Wb, m));
+    for (int j = 0; j < m; j++) SQD_TRY(dot_col(j + 1, j));
+
+    std::vector<double> theta(M), theta_old(k, INFINITY), rn2(k), rn(k);
+    int it = 0;
+    int status = SQD_OK;
+    for (;;) {
+        SQD_TRY(launch_jacobi_eigh(ctx, w.G, M, m, w.evals, w.evecs));
+        SQD_TRY(launch_combine(ctx, w.Vb, N, m, w.evecs, m, k, w.X, N, N));
+        SQD_TRY(launch_combine(ctx, w.Wb, N, m, w.evecs, m, k, w.R, N, N));
+        SQD_TRY(launch_residual(ctx, w.X, w.R, w.evals, k, N, w.R));
+        for (int j = 0; j < k; j++)
+            SQD_TRY(launch_multidot(ctx, w.R + (int64_t)j * N, N, 1, w.R + (int64_t)j * N, N,
+                                    w.partial, nblk, w.dots + j));
+        SQD_CUDA(ctx, cudaMemcpyAsync(theta.data(), w.evals, sizeof(double) * m,
+                                      cudaMemcpyDeviceToHost, st));
+        SQD_CUDA(ctx, cudaMemcpyAsync(rn2.data(), w.dots, sizeof(double) * k,
+                                      cudaMemcpyDeviceToHost, st));
+        SQD_CUDA(ctx, cudaStreamSynchronize(st));
+        bool all = true;
+        std::vector<int> todo;
+        for (int j = 0; j < k; j++) {
+            rn[j] = std::sqrt(std::max(rn2[j], 0.0));
+            bool c = rn[j] <= o->tol_residual && std::fabs(theta[j] - theta_old[j]) <= o->tol_energy;
+            if (!c) {
+                all = false;
+                todo.push_back(j);
+            }
+        }
+        if (all) break;
+        if (it >= o->max_iter) {
+            status = SQD_ENOTCONVERGED;
+            break;
+        }
+        it++;
+        for (int j = 0; j < k; j++) theta_old[j] = theta[j];
+        if (m + (int)todo.size() > M) {
+            // thick restart on the 2k lowest Ritz vectors
+            int m2 = std::min(k2, m);
+            SQD_TRY(launch_combine(ctx, w.Vb, N, m, w.evecs, m, m2, w.Tmp, N, N));
+            SQD_CUDA(ctx, cudaMemcpyAsync(w.Vb, w.Tmp, sizeof(double) * m2 * N,
+                                          cudaMemcpyDeviceToDevice, st));
+            SQD_TRY(launch_combine(ctx, w.Wb, N, m, w.evecs, m, m2, w.Tmp, N, N));
+            SQD_CUDA(ctx, cudaMemcpyAsync(w.Wb, w.Tmp, sizeof(double) * m2 * N,
+                                          cudaMemcpyDeviceToDevice, st));
+            m = m2;
+            for (int j = 0; j < m; j++) SQD_TRY(dot_col(j + 1, j));
+        }
+        int m_old = m;
+        for (int j : todo) {
+            double *v = w.Vb + (int64_t)m * N;
+            SQD_TRY(launch_precondition(ctx, w.R + (int64_t)j * N, t->diag, theta[j],
+                                        o->precond_floor, N, v));
+            double n2 = 0.0;
+            SQD_TRY(orthonormalize(m, &n2));
+            if (!(std::sqrt(n2) >= 1e-12)) continue;  // dropped
+            SQD_TRY(launch_scale(ctx, v, N, w.dots, 1));
+            m++;
+        }
+        if (m == m_old) {
+            bool res_ok = true;
+            for (int j = 0; j < k; j++) res_ok = res_ok && rn[j] <= o->tol_residual;
+            if (!res_ok) status = SQD_EBREAKDOWN;
+            break;
+        }
+        SQD_TRY(sigma_impl(ctx, t, w.Vb + (int64_t)m_old * N, w.Wb + (int64_t)m_old * N,
+                           m - m_old));
+        for (int j = m_old; j < m; j++) SQD_TRY(dot_col(j + 1, j));
+    }
+    // outputs: Ritz vectors with the phase fixed, energies, residuals
+    SQD_CUDA(ctx, cudaMemcpyAsync(d_C, w.X, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, st));
+    SQD_TRY(launch_fix_phase(ctx, d_C, N, k, N, w.phase));
+    SQD_CUDA(ctx, cudaStreamSynchronize(st));
+    for (int j = 0; j < k; j++) {
+        h_energies[j] = theta[j];
+        if (h_res) h_res[j] = rn[j];
+    }
+    if (h_iters) *h_iters = it;
+    if (status == SQD_ENOTCONVERGED)
+        return sqd_fail(ctx, status, "Davidson did not converge in %d iterations", it);
+    if (status == SQD_EBREAKDOWN)
+        return sqd_fail(ctx, status, "Davidson basis could not be extended");
+    return SQD_OK;
+}
+
+int sqd_davidson(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, double *h_energies,
+                 double *d_C, int *h_iters, double *h_res) {
+    if (!ctx || !t || !o) return fail_noctx(SQD_EINVAL, "sqd_davidson: NULL argument");
+    if (!h_energies || !d_C) return sqd_fail(ctx, SQD_EINVAL, "NULL output");
+    const int64_t N = t->a.n * t->b->n;
+    if (o->nroots < 1 || o->nroots > 32 || o->nroots > N)
+        return sqd_fail(ctx, SQD_EINVAL, "nroots must be in [1, min(32, dimension)]");
+    if (o->max_iter < 0 || !(o->tol_energy >= 0) || !(o->tol_residual >= 0) ||
+        !(o->precond_floor > 0) || o->max_subspace < 0)
+        return sqd_fail(ctx, SQD_EINVAL, "invalid Davidson options");
+    SQD_TRY(use_device(ctx));
+    return davidson_impl(ctx, t, o, h_energies, d_C, h_iters, h_res);
+}
+
+// ----------------------------------------------------------------- RDMs --
+
+int sqd_rdm(sqd_ctx *ctx, sqd_tables *t, const double *d_C, double *d_rdm1, double *d_rdm2) {
+    if (!ctx || !t) return fail_noctx(SQD_EINVAL, "sqd_rdm: NULL argument");
+    if (!d_C || !d_rdm1) return sqd_fail(ctx, SQD_EINVAL, "NULL buffer");
+    SQD_TRY(use_device(ctx));
+    return launch_rdm(ctx, t, d_C, d_rdm1, d_rdm2);
+}
+
+}  // extern "C"

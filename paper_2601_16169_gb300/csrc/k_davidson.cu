@@ -1,0 +1,483 @@
+// Device kernels of the Davidson driver: block dot products, basis updates,
+// residuals, the diagonal preconditioner, guess selection, sign fixing and a
+// one-block parallel (round-robin) Jacobi eigensolver for the small
+// Rayleigh-Ritz matrix.  All arithmetic is FP64; reductions run in a fixed
+// order so results do not depend on scheduling.
+#include <cmath>
+
+#include "sqd_internal.cuh"
+
+#define RED_THREADS 256
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) r += sh[i];
+    }
+    __syncthreads();
+    return r;  // valid in thread 0
+}
+
+int multidot_blocks(int64_t n) {
+    int64_t b = (n + 4095) / 4096;
+    if (b > 1024) b = 1024;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// partial[i * nblk + blk] = sum over this block's slice of A_i[n] * x[n]
+__global__ void __launch_bounds__(RED_THREADS)
+    k_multidot_partial(const double *__restrict__ A, int64_t lda, int m,
+                       const double *__restrict__ x, int64_t n, double *__restrict__ partial) {
+    __shared__ double sh[32];
+    int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    int64_t lo = per * blockIdx.x, hi = min(n, lo + per);
+    for (int i = 0; i < m; i++) {
+        const double *a = A + (int64_t)i * lda;
+        double s = 0.0;
+        for (int64_t j = lo + threadIdx.x; j < hi; j += RED_THREADS) s = fma(a[j], x[j], s);
+        double t = block_sum(s, sh);
+        if (threadIdx.x == 0) partial[(int64_t)i * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+__global__ void k_multidot_final(const double *__restrict__ partial, int nblk, int m,
+                                 double *__restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; b++) s += partial[(int64_t)i * nblk + b];
+    out[i] = s;
+}
+
+int launch_multidot(sqd_ctx *ctx, const double *A, int64_t lda, int m, const double *x,
+                    int64_t n, double *partial, int nblk, double *out) {
+    if (m == 0) return SQD_OK;
+    k_multidot_partial<<<nblk, RED_THREADS, 0, ctx->stream>>>(A, lda, m, x, n, partial);
+    SQD_LAUNCHED(ctx);
+    k_multidot_final<<<(m + 63) / 64, 64, 0, ctx->stream>>>(partial, nblk, m, out);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// x[n] -= sum_i A_i[n] c[i]
+__global__ void k_gemv_sub(const double *__restrict__ A, int64_t lda, int m,
+                           const double *__restrict__ c, double *__restrict__ x, int64_t n) {
+    __shared__ double cs[256];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) cs[i] = c[i];
+    __syncthreads();
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < m; i++) s = fma(A[(int64_t)i * lda + j], cs[i], s);
+        x[j] -= s;
+    }
+}
+
+int launch_gemv_sub(sqd_ctx *ctx, const double *A, int64_t lda, int m, const double *c,
+                    double *x, int64_t n) {
+    if (m == 0 || n == 0) return SQD_OK;
+    if (m > 256) return sqd_fail(ctx, SQD_EINVAL, "basis too large");
+    unsigned g = grid_1d(n, 256);
+    if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
+    k_gemv_sub<<<g, 256, 0, ctx->stream>>>(A, lda, m, c, x, n);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// out_j[n] = sum_i A_i[n] Y[i + j*ldy], j < k
+__global__ void k_combine(const double *__restrict__ A, int64_t lda, int m,
+                          const double *__restrict__ Y, int ldy, int k, double *__restrict__ out,
+                          int64_t ldo, int64_t n) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        for (int j0 = 0; j0 < k; j0 += 8) {
+            double acc[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) acc[q] = 0.0;
+            int jn = min(8, k - j0);
+            for (int i = 0; i < m; i++) {
+                double a = A[(int64_t)i * lda + p];
+#pragma unroll
+                for (int q = 0; q < 8; q++)
+                    if (q < jn) acc[q] = fma(a, __ldg(Y + i + (int64_t)(j0 + q) * ldy), acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                if (q < jn) out[(int64_t)(j0 + q) * ldo + p] = acc[q];
+        }
+    }
+}
+
+int launch_combine(sqd_ctx *ctx, const double *A, int64_t lda, int m, const double *Y, int ldy,
+                   int k, double *out, int64_t ldo, int64_t n) {
+    if (k == 0 || n == 0) return SQD_OK;
+    unsigned g = grid_1d(n, 256);
+    if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
+    k_combine<<<g, 256, 0, ctx->stream>>>(A, lda, m, Y, ldy, k, out, ldo, n);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// R_j = WY_j - theta_j X_j
+__global__ void k_residual(const double *__restrict__ X, const double *__restrict__ WY,
+                           const double *__restrict__ theta, int k, int64_t n,
+                           double *__restrict__ R) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n * k;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int j = (int)(p / n);
+        R[p] = fma(-theta[j], X[p], WY[p]);
+    }
+}
+
+int launch_residual(sqd_ctx *ctx, const double *X, const double *WY, const double *theta,
+                    int k, int64_t n, double *R) {
+    if (k == 0 || n == 0) return SQD_OK;
+    unsigned g = grid_1d(n * k, 256);
+    if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
+    k_residual<<<g, 256, 0, ctx->stream>>>(X, WY, theta, k, n, R);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// T = R / (theta - diag), |denominator| clamped to floor_ (sign kept, + for 0)
+__global__ void k_precondition(const double *__restrict__ R, const double *__restrict__ diag,
+                               double theta, double floor_, int64_t n, double *__restrict__ T) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double d = theta - diag[p];
+        if (fabs(d) < floor_) d = (d < 0.0) ? -floor_ : floor_;
+        T[p] = R[p] / d;
+    }
+}
+
+int launch_precondition(sqd_ctx *ctx, const double *R, const double *diag, double theta,
+                        double floor_, int64_t n, double *T) {
+    if (n == 0) return SQD_OK;
+    unsigned g = grid_1d(n, 256);
+    if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
+    k_precondition<<<g, 256, 0, ctx->stream>>>(R, diag, theta, floor_, n, T);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// x *= s  (invert_sqrt: x *= 1/sqrt(s))
+__global__ void k_scale(double *__restrict__ x, int64_t n, const double *__restrict__ s,
+                        int invert_sqrt) {
+    double f = invert_sqrt ? 1.0 / sqrt(*s) : *s;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        x[p] *= f;
+}
+
+int launch_scale(sqd_ctx *ctx, double *x, int64_t n, const double *s_dev, int invert_sqrt) {
+    if (n == 0) return SQD_OK;
+    unsigned g = grid_1d(n, 256);
+    if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
+    k_scale<<<g, 256, 0, ctx->stream>>>(x, n, s_dev, invert_sqrt);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// ------------------------------------------------------ Jacobi (1 block) --
+// Symmetric eigenproblem of the m x m Rayleigh-Ritz matrix, m <= 128.
+// Parallel cyclic Jacobi with the round-robin pair schedule: each step
+// rotates m/2 disjoint (p,q) pairs chosen to zero A_pq (Golub & Van Loan,
+// symmetric Schur decomposition 2x2), then applies all column rotations and
+// all row rotations.  Sweeps until the off-diagonal norm is negligible.
+// Output: evals ascending, evecs column-major (evecs[i + j*m] = Y_ij).
+
+#define JAC_MAX 112
+
+__global__ void __launch_bounds__(1024) k_jacobi(const double *__restrict__ G, int ldg, int m,
+                                                 double *__restrict__ evals,
+                                                 double *__restrict__ evecs) {
+    // A and Q live in dynamic shared memory, (M) x (M+1) doubles each
+    extern __shared__ double jac_sh[];
+    __shared__ double cs[JAC_MAX / 2], sn[JAC_MAX / 2];
+    __shared__ int pp[JAC_MAX / 2], qq[JAC_MAX / 2];
+    __shared__ double red[32];
+    __shared__ int done;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int M = (m + 1) & ~1;  // even size; a padding row/col stays zero
+    const int LD = M + 1;
+    double *Ab = jac_sh, *Qb = jac_sh + (size_t)M * LD;
+#define A(i, j) Ab[(i) * LD + (j)]
+#define Q(i, j) Qb[(i) * LD + (j)]
+    // only the upper triangle G[i + j*ldg], i <= j, is read
+    for (int t = tid; t < M * M; t += nt) {
+        int i = t / M, j = t % M;
+        double v = 0.0;
+        if (i < m && j < m) v = (i <= j) ? G[i + (int64_t)j * ldg] : G[j + (int64_t)i * ldg];
+        A(i, j) = v;
+        Q(i, j) = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const int npair = M / 2;
+    for (int sweep = 0; sweep < 60; sweep++) {
+        // convergence: off-diagonal Frobenius norm vs diagonal
+        double off = 0.0, dia = 0.0;
+        for (int t = tid; t < M * M; t += nt) {
+            int i = t / M, j = t % M;
+            double v = A(i, j);
+            if (i != j) off += v * v; else dia += v * v;
+        }
+        double offs = block_sum(off, red);
+        double dias = block_sum(dia, red);
+        if (tid == 0) done = (offs <= 1e-30 * dias || offs == 0.0) ? 1 : 0;
+        __syncthreads();
+        if (done) break;
+        for (int step = 0; step < M - 1; step++) {
+            if (tid < npair) {
+                // round-robin: player M-1 fixed, the others rotate
+                int a, b;
+                if (tid == 0) {
+                    a = step;
+                    b = M - 1;
+                } else {
+                    a = (step + tid) % (M - 1);
+                    b = (step + M - 1 - tid) % (M - 1);
+                }
+                int p = min(a, b), q = max(a, b);
+                double apq = A(p, q);
+                double c = 1.0, s = 0.0;
+                if (apq != 0.0) {
+                    double tau = (A(q, q) - A(p, p)) / (2.0 * apq);
+                    double t = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau))
+                                            : -1.0 / (-tau + sqrt(1.0 + tau * tau));
+                    c = 1.0 / sqrt(1.0 + t * t);
+                    s = t * c;
+                }
+                pp[tid] = p;
+                qq[tid] = q;
+                cs[tid] = c;
+                sn[tid] = s;
+            }
+            __syncthreads();
+            // columns: A <- A J, Q <- Q J
+            for (int t = tid; t < M * npair; t += nt) {
+                int r = t / npair, k = t % npair;
+                int p = pp[k], q = qq[k];
+                double c = cs[k], s = sn[k];
+                double ap = A(r, p), aq = A(r, q);
+                A(r, p) = c * ap - s * aq;
+                A(r, q) = s * ap + c * aq;
+                double qp = Q(r, p), qv = Q(r, q);
+                Q(r, p) = c * qp - s * qv;
+                Q(r, q) = s * qp + c * qv;
+            }
+            __syncthreads();
+            // rows: A <- J^T A
+            for (int t = tid; t < M * npair; t += nt) {
+                int col = t / npair, k = t % npair;
+                int p = pp[k], q = qq[k];
+                double c = cs[k], s = sn[k];
+                double ap = A(p, col), aq = A(q, col);
+                A(p, col) = c * ap - s * aq;
+                A(q, col) = s * ap + c * aq;
+            }
+            __syncthreads();
+        }
+    }
+    // sort ascending (selection of the order by one thread), write out
+    __shared__ int order[JAC_MAX];
+    if (tid == 0) {
+        for (int i = 0; i < m; i++) order[i] = i;
+        for (int i = 0; i < m; i++) {
+            int best = i;
+            for (int j = i + 1; j < m; j++) {
+                double dj = A(order[j], order[j]), db = A(order[best], order[best]);
+                if (dj < db || (dj == db && order[j] < order[best])) best = j;
+            }
+            int tmp = order[i];
+            order[i] = order[best];
+            order[best] = tmp;
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < m * m; t += nt) {
+        int i = t % m, j = t / m;  // evecs[i + j*m] = Q(i, order[j])
+        evecs[i + (int64_t)j * m] = Q(i, order[j]);
+    }
+    for (int j = tid; j < m; j += nt) evals[j] = A(order[j], order[j]);
+}
+
+int launch_jacobi_eigh(sqd_ctx *ctx, const double *G, int ldg, int m, double *evals,
+                       double *evecs) {
+    if (m < 1 || m > JAC_MAX) return sqd_fail(ctx, SQD_EINVAL, "subspace size %d out of range", m);
+    int M = (m + 1) & ~1;
+    size_t shm = sizeof(double) * 2 * (size_t)M * (M + 1);
+    SQD_CUDA(ctx, cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(double) * 2 * JAC_MAX * (JAC_MAX + 1))));
+    k_jacobi<<<1, 1024, shm, ctx->stream>>>(G, ldg, m, evals, evecs);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// ------------------------------------------------------- guess selection --
+// idx[t] = index of the t-th smallest diag entry in (value, index) order.
+struct vi {
+    double v;
+    int64_t i;
+};
+
+__device__ __forceinline__ bool vi_less(double v1, int64_t i1, double v2, int64_t i2) {
+    return v1 < v2 || (v1 == v2 && i1 < i2);
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+    k_argmin_partial(const double *__restrict__ d, int64_t n, double lv, int64_t li,
+                     double *__restrict__ pv, int64_t *__restrict__ pi) {
+    __shared__ double sv[RED_THREADS];
+    __shared__ int64_t si[RED_THREADS];
+    double bv = INFINITY;
+    int64_t bi = -1;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double v = d[p];
+        bool after = (li < 0) || vi_less(lv, li, v, p);
+        if (after && (bi < 0 || vi_less(v, p, bv, bi))) {
+            bv = v;
+            bi = p;
+        }
+    }
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            double v2 = sv[threadIdx.x + o];
+            int64_t i2 = si[threadIdx.x + o];
+            if (i2 >= 0 && (si[threadIdx.x] < 0 || vi_less(v2, i2, sv[threadIdx.x], si[threadIdx.x]))) {
+                sv[threadIdx.x] = v2;
+                si[threadIdx.x] = i2;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        pv[blockIdx.x] = sv[0];
+        pi[blockIdx.x] = si[0];
+    }
+}
+
+__global__ void k_argmin_final(const double *pv, const int64_t *pi, int nblk, int t,
+                               int64_t *idx, double *lastv) {
+    double bv = INFINITY;
+    int64_t bi = -1;
+    for (int b = 0; b < nblk; b++)
+        if (pi[b] >= 0 && (bi < 0 || vi_less(pv[b], pi[b], bv, bi))) {
+            bv = pv[b];
+            bi = pi[b];
+        }
+    idx[t] = bi;
+    lastv[0] = bv;
+}
+
+int launch_argmin_k(sqd_ctx *ctx, const double *d, int64_t n, int k, int64_t *idx_dev) {
+    int nblk = 4 * ctx->sm_count;
+    double *pv = nullptr, *lastv = nullptr;
+    int64_t *pi = nullptr;
+    SQD_CUDA(ctx, cudaMallocAsync((void **)&pv, sizeof(double) * (nblk + 1), ctx->stream));
+    SQD_CUDA(ctx, cudaMallocAsync((void **)&pi, sizeof(int64_t) * nblk, ctx->stream));
+    lastv = pv + nblk;
+    double hv = 0.0;
+    int64_t hi = -1;
+    for (int t = 0; t < k; t++) {
+        k_argmin_partial<<<nblk, RED_THREADS, 0, ctx->stream>>>(d, n, hv, hi, pv, pi);
+        SQD_LAUNCHED(ctx);
+        k_argmin_final<<<1, 1, 0, ctx->stream>>>(pv, pi, nblk, t, idx_dev, lastv);
+        SQD_LAUNCHED(ctx);
+        SQD_CUDA(ctx, cudaMemcpyAsync(&hv, lastv, sizeof(double), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        SQD_CUDA(ctx, cudaMemcpyAsync(&hi, idx_dev + t, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        SQD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (hi < 0) return sqd_fail(ctx, SQD_EINVAL, "fewer determinants than roots");
+    }
+    SQD_CUDA(ctx, cudaFreeAsync(pv, ctx->stream));
+    SQD_CUDA(ctx, cudaFreeAsync(pi, ctx->stream));
+    return SQD_OK;
+}
+
+__global__ void k_set_unit(double *V, int64_t ld, int k, const int64_t *idx) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < k) V[(int64_t)j * ld + idx[j]] = 1.0;
+}
+
+int launch_set_unit(sqd_ctx *ctx, double *V, int64_t ld, int k, const int64_t *idx_dev) {
+    k_set_unit<<<1, 128, 0, ctx->stream>>>(V, ld, k, idx_dev);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// ---------------------------------------------------------------- phase --
+// Flip each vector so that its largest-magnitude component (lowest index on
+// ties) is positive.
+__global__ void __launch_bounds__(RED_THREADS)
+    k_absmax_partial(const double *__restrict__ x, int64_t n, double *__restrict__ pv,
+                     int64_t *__restrict__ pi) {
+    __shared__ double sv[RED_THREADS];
+    __shared__ int64_t si[RED_THREADS];
+    double bv = -1.0;
+    int64_t bi = -1;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double v = fabs(x[p]);
+        if (v > bv) {  // first (lowest) index wins ties within a thread
+            bv = v;
+            bi = p;
+        }
+    }
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            double v2 = sv[threadIdx.x + o];
+            int64_t i2 = si[threadIdx.x + o];
+            if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 >= 0 && i2 < si[threadIdx.x])) {
+                sv[threadIdx.x] = v2;
+                si[threadIdx.x] = i2;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        pv[blockIdx.x] = sv[0];
+        pi[blockIdx.x] = si[0];
+    }
+}
+
+__global__ void k_phase_final(const double *x, const double *pv, const int64_t *pi, int nblk,
+                              double *sign_out) {
+    double bv = -1.0;
+    int64_t bi = -1;
+    for (int b = 0; b < nblk; b++)
+        if (pv[b] > bv || (pv[b] == bv && pi[b] >= 0 && pi[b] < bi)) {
+            bv = pv[b];
+            bi = pi[b];
+        }
+    *sign_out = (bi >= 0 && x[bi] < 0.0) ? -1.0 : 1.0;
+}
+
+int launch_fix_phase(sqd_ctx *ctx, double *X, int64_t ld, int k, int64_t n, double *work_dev) {
+    int nblk = 4 * ctx->sm_count;
+    double *pv = work_dev;                          // nblk
+    int64_t *pi = (int64_t *)(work_dev + nblk);     // nblk
+    double *sg = work_dev + 2 * nblk;               // 1
+    for (int j = 0; j < k; j++) {
+        double *x = X + (int64_t)j * ld;
+        k_absmax_partial<<<nblk, RED_THREADS, 0, ctx->stream>>>(x, n, pv, pi);
+        SQD_LAUNCHED(ctx);
+        k_phase_final<<<1, 1, 0, ctx->stream>>>(x, pv, pi, nblk, sg);
+        SQD_LAUNCHED(ctx);
+        SQD_TRY(launch_scale(ctx, x, n, sg, 0));
+    }
+    return SQD_OK;
+}

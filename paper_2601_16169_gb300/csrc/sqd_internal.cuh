@@ -1,0 +1,198 @@
+// Internal declarations of the sm_103a SQD library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sqd.h"
+
+// Kernel classes for the measurement counters (sqd_profile_*).
+enum prof_class {
+    PROF_SAME_ALPHA = 0,  // k_same_spin on C with the alpha tables (+ diagonal)
+    PROF_SAME_BETA,       // k_same_spin on C^T with the beta tables
+    PROF_ALPHA_BETA,      // k_alpha_beta (paired singles)
+    PROF_TRANSPOSE,       // C -> C^T and the transposed add-back
+    PROF_TABLES,          // excitation tables, string terms, diagonal
+    PROF_STRINGS,         // string filtering, sort, scan
+    PROF_DAVIDSON,        // Davidson vector kernels and the Jacobi solver
+    PROF_RDM,             // density matrices
+    PROF_NCLASS
+};
+
+struct prof_rec {
+    int cls;
+    cudaEvent_t a, b;
+};
+
+struct sqd_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    std::string err;
+    // measurement counters
+    int64_t launches = 0;                // kernel launches since the last reset
+    bool prof = false;                   // event timing enabled
+    int open_cls = -1;
+    std::vector<prof_rec> recs;          // timed regions (event pairs)
+    std::vector<cudaEvent_t> pool;       // free events
+    int64_t cls_launches[PROF_NCLASS] = {0};
+    double cls_flops[PROF_NCLASS] = {0};
+    double cls_bytes[PROF_NCLASS] = {0};
+    double cls_ms[PROF_NCLASS] = {0};
+};
+
+// Time the launches between prof_begin/prof_end as one region of class cls
+// (no-op unless profiling is enabled) and book its algorithmic work.
+void prof_begin(sqd_ctx *ctx, int cls);
+void prof_end(sqd_ctx *ctx, double flops, double bytes);
+
+// Excitation tables of one string set (one spin).
+struct spin_tables {
+    int64_t n = 0;   // strings
+    int ne = 0;      // electrons
+    uint64_t *str = nullptr;  // sorted strings, device
+
+    // singles CSR (entries of a row sorted by target)
+    int64_t nnz1 = 0;
+    int64_t *off1 = nullptr;   // n+1
+    int32_t *tgt1 = nullptr;   // target string index
+    uint16_t *pq1 = nullptr;   // p*norb+q (p created, q annihilated)
+    int8_t *sgn1 = nullptr;    // <J|a+_p a_q|I>
+    double *val1 = nullptr;    // <I|H_s|J>
+
+    // doubles CSR
+    int64_t nnz2 = 0;
+    int64_t *off2 = nullptr;
+    int32_t *tgt2 = nullptr;
+    uint32_t *orb2 = nullptr;  // i | j<<8 | a<<16 | b<<24
+    int8_t *sgn2 = nullptr;
+    double *val2 = nullptr;
+
+    double *energy = nullptr;  // E_s(I) = <I|H_s|I>
+    double *W = nullptr;       // [norb*norb][n]: sum_{l in I} (pq|ll)
+    double *u = nullptr;       // [n][norb]: sum_{l in I} (kk|ll)
+
+    std::vector<int64_t> h_off1;  // host copy of off1 (scheduling)
+    int64_t max1 = 0, max2 = 0;
+};
+
+// Work decomposition of the alpha-beta (paired singles) kernel.
+struct ab_schedule {
+    // beta chunks: rows [rows[c], rows[c+1]) of the beta singles table
+    int nchunks = 0;
+    int64_t *chunk_rows = nullptr;  // device, nchunks+1
+    // alpha row groups: [grp[g], grp[g+1])
+    int ngroups = 0;
+    int64_t *group_rows = nullptr;  // device, ngroups+1
+};
+
+struct sqd_tables {
+    sqd_ctx *ctx = nullptr;
+    int norb = 0;
+    double ecore = 0.0;
+    double *h = nullptr;  // device copy
+    double *V = nullptr;  // device copy
+    spin_tables a, b_own;
+    spin_tables *b = nullptr;  // == &a when shared
+    bool shared = false;
+    double *diag = nullptr;    // [na][nb]
+    ab_schedule ab;
+    // sigma scratch
+    double *scratch_t = nullptr;  // C^T
+    double *scratch_s = nullptr;  // (sigma_bb)^T
+    int64_t bytes = 0;
+};
+
+// ---- error helpers -----------------------------------------------------
+int sqd_fail(sqd_ctx *ctx, int code, const char *fmt, ...);
+#define SQD_CUDA(ctx, call)                                                   \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess)                                                \
+            return sqd_fail((ctx), e_ == cudaErrorMemoryAllocation ? SQD_ENOMEM \
+                                                                    : SQD_ECUDA, \
+                            "%s failed: %s (%s:%d)", #call,                   \
+                            cudaGetErrorString(e_), __FILE__, __LINE__);      \
+    } while (0)
+// after every kernel launch: count it and surface launch errors
+#define SQD_LAUNCHED(ctx)                                                     \
+    do {                                                                      \
+        (ctx)->launches++;                                                    \
+        SQD_CUDA((ctx), cudaGetLastError());                                  \
+    } while (0)
+#define SQD_TRY(call)          \
+    do {                       \
+        int r_ = (call);       \
+        if (r_ != SQD_OK)      \
+            return r_;         \
+    } while (0)
+
+static inline unsigned grid_1d(int64_t n, int threads) {
+    int64_t g = (n + threads - 1) / threads;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+// ---- launchers (implemented in the k_*.cu files) ------------------------
+// strings / sort / scan
+int launch_filter_flags(sqd_ctx *, const uint64_t *raw, int64_t n, int norb, int nelec,
+                        int64_t *flags);
+int launch_exclusive_scan(sqd_ctx *, const int64_t *in, int64_t *out, int64_t n,
+                          int64_t *total_dev);
+int launch_scatter_flagged(sqd_ctx *, const uint64_t *in, const int64_t *flags,
+                           const int64_t *pos, int64_t n, uint64_t *out);
+int launch_fill_u64(sqd_ctx *, uint64_t *p, int64_t n, uint64_t v);
+int launch_bitonic_sort_u64(sqd_ctx *, uint64_t *keys, int64_t n_pow2);
+int launch_unique_flags(sqd_ctx *, const uint64_t *sorted, int64_t n, int64_t *flags);
+int launch_check_sorted_unique(sqd_ctx *, const uint64_t *s, int64_t n, int norb, int ne,
+                               int *bad_dev);
+int launch_check_integrals(sqd_ctx *, const double *h, const double *V, int norb,
+                           double *res_dev);
+
+// tables
+int launch_count_excitations(sqd_ctx *, const uint64_t *s, int64_t n, int norb, int kind,
+                             int64_t *counts);
+int launch_fill_excitations(sqd_ctx *, const uint64_t *s, int64_t n, int norb, int kind,
+                            const int64_t *off, int64_t *cursor, uint64_t *keys);
+int launch_finalize_singles(sqd_ctx *, const uint64_t *s, int norb, const uint64_t *keys,
+                            int64_t nnz, const double *h, const double *V, int32_t *tgt,
+                            uint16_t *pq, int8_t *sgn, double *val);
+int launch_finalize_doubles(sqd_ctx *, const uint64_t *s, int norb, const uint64_t *keys,
+                            int64_t nnz, const double *V, int32_t *tgt, uint32_t *orb,
+                            int8_t *sgn, double *val);
+int launch_string_terms(sqd_ctx *, const uint64_t *s, int64_t n, int norb, const double *h,
+                        const double *V, double *energy, double *W, double *u);
+int launch_diagonal(sqd_ctx *, const spin_tables *a, const spin_tables *b, int norb,
+                    double ecore, const uint64_t *sa, double *diag);
+
+// sigma
+int launch_same_spin(sqd_ctx *, const spin_tables *rows, const spin_tables *cols,
+                     int64_t nrows, int64_t ncols, const double *C, double *S,
+                     const double *diag);
+int launch_alpha_beta(sqd_ctx *, const sqd_tables *t, const double *C, double *S);
+int launch_transpose(sqd_ctx *, const double *in, double *out, int64_t rows, int64_t cols,
+                     bool add);
+
+// davidson helpers
+int launch_multidot(sqd_ctx *, const double *A, int64_t lda, int m, const double *x,
+                    int64_t n, double *partial, int nblk, double *out);
+int multidot_blocks(int64_t n);
+int launch_gemv_sub(sqd_ctx *, const double *A, int64_t lda, int m, const double *c,
+                    double *x, int64_t n);
+int launch_combine(sqd_ctx *, const double *A, int64_t lda, int m, const double *Y,
+                   int ldy, int k, double *out, int64_t ldo, int64_t n);
+int launch_residual(sqd_ctx *, const double *X, const double *WY, const double *theta,
+                    int k, int64_t n, double *R);
+int launch_precondition(sqd_ctx *, const double *R, const double *diag, double theta,
+                        double floor_, int64_t n, double *T);
+int launch_scale(sqd_ctx *, double *x, int64_t n, const double *s_dev, int invert_sqrt);
+int launch_jacobi_eigh(sqd_ctx *, const double *G, int ldg, int m, double *evals,
+                       double *evecs);
+int launch_argmin_k(sqd_ctx *, const double *d, int64_t n, int k, int64_t *idx_dev);
+int launch_set_unit(sqd_ctx *, double *V, int64_t ld, int k, const int64_t *idx_dev);
+int launch_fix_phase(sqd_ctx *, double *X, int64_t ld, int k, int64_t n, double *work_dev);
+
+// rdm
+int launch_rdm(sqd_ctx *, const sqd_tables *t, const double *C, double *rdm1, double *rdm2);
