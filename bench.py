@@ -1,0 +1,449 @@
+#!/usr/bin/env python
+"""Benchmark of the SQD hot path (arXiv 2601.16169) on GB300.
+
+One step = the whole hot path on one synthetic workload: filter the raw
+sampled strings (sqd_build_strings), build the excitation tables and the
+diagonal (sqd_excitation_tables), and run the device Davidson solve to
+convergence (sqd_davidson, whose cost is the sigma = H C products).
+
+The headline metric is sigma throughput, H.C applications per second (one
+application = sigma of one vector over all n_alpha * n_beta determinants),
+over whole steps; time-to-converged E is reported beside it.  Inputs (raw
+strings, h, V) are resident on the device when the timed region starts;
+the e2e entry repeats the steps through the same public API from pinned host
+buffers with the copies inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank solves its own replica of the workload
+(the path does not shard: replicas only) and rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import sqd_inputs as si  # noqa: E402
+
+METRIC = "Davidson sigma H·C/s and time-to-converged E (FP64) vs HBM roofline, 1×GB300"
+UNIT = "H·C/s"
+
+# Davidson settings per workload (convergence readings of the build)
+SOLVE = {
+    "scale36": dict(nroots=1, tol_residual=1e-5, tol_energy=1e-8, max_iter=200),
+    "h2o29": dict(nroots=8, tol_residual=1e-8, tol_energy=1e-8, max_iter=200),
+    "adjoint29": dict(nroots=1, tol_residual=1e-5, tol_energy=1e-8, max_iter=200),
+    "full8": dict(nroots=1, tol_residual=1e-8, tol_energy=1e-10, max_iter=200),
+}
+DESCR = {
+    "scale36": "scale36: norb=36, 15+15 electrons, 20000 shared sampled strings "
+               "(P(k) ~ 1/(1+exp((k-15)/2.5))), 4.0e8 determinants, rank-72 integrals, "
+               "ground state (|dE| <= 1e-8, ||r|| <= 1e-5)",
+    "h2o29": "h2o29: norb=29, 5+5 electrons, 2000 shared sampled strings (P(k) ~ exp(-k/6)), "
+             "4.0e6 determinants, rank-58 integrals, 8 roots to ||r|| <= 1e-8",
+    "adjoint29": "adjoint29: norb=29, 5+5 electrons, 5000 shared strings, 2.5e7 determinants",
+    "full8": "full8: norb=8, 4+4 electrons, full space, 4900 determinants",
+}
+
+# FP64 peak for the ALU roofline: 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM
+# (the nominal 1.25 TFLOP/s FP64 of GB300 at its maximum SM clock).
+FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="h2o29", choices=sorted(SOLVE))
+    p.add_argument("--sigma-extra", default="scale36",
+                   help="workload whose sigma-only throughput is added to the line "
+                        "('none' to skip)")
+    p.add_argument("--e2e-steps", type=int, default=None)
+    p.add_argument("--cpu-rows", type=int, default=None,
+                   help="rows of sigma in the CPU-baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--mode", default="solve", choices=["solve", "sigma"],
+                   help="solve: the whole path per step; sigma: one sigma = H C per step "
+                        "on prebuilt tables (kernel-only number, used for profiling)")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------- clocks ------
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------ CPU baseline ------
+
+def cpu_baseline(w, rows_n):
+    """The oracle (as it stands) timed on the host cores on a bounded sample:
+    rows_n seeded rows of one sigma of the workload.  Returns H.C/s
+    (rows/s divided by the determinant count) and the sample description."""
+    import oracle
+    oracle.lib()
+    N = w.ndet
+    C = si.random_vectors(1, N, 13)[0]
+    rows = np.sort(np.random.default_rng(0).choice(N, size=min(rows_n, N), replace=False))
+    t0 = time.perf_counter()
+    oracle.sigma(w.norb, w.h, w.V, 0.0, w.strings_a, w.strings_b, C, rows=rows)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": (len(rows) / dt) / N, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d seeded rows of one sigma of %s (%.1f s incl. neighbour lists); "
+                      "H.C/s = rows/s / %d determinants" % (len(rows), w.name, dt, N),
+            "seconds": dt}
+
+
+def default_cpu_rows(name):
+    return {"scale36": 400000, "h2o29": 4000000, "adjoint29": 2000000, "full8": 4900}[name]
+
+
+# ------------------------------------------------------------ ours -------
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("k_sigma.cu",):
+        h.update(open(os.path.join(ROOT, "paper_2601_16169_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if "=" in line and not line.lstrip().startswith("#"):
+            k, v = line.split("=", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha") != kernel_source_hash():
+        return None
+    v = vals.get("%s.bytes_per_launch" % kernel)
+    return float(v) if v else None
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2601_16169_gb300 as sqd
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = si.workload(args.workload)
+    opts = SOLVE[args.workload]
+    ctx = sqd.Context(local_rank)
+    stream = torch.cuda.current_stream(dev)
+
+    raw_h = torch.from_numpy(w.raw_a.view(np.int64).copy()).pin_memory()
+    h_h = torch.from_numpy(w.h.copy()).pin_memory()
+    V_h = torch.from_numpy(w.V.copy()).pin_memory()
+    raw_d, h_d, V_d = raw_h.to(dev), h_h.to(dev), V_h.to(dev)
+    bytes_in = raw_h.numel() * 8 + h_h.numel() * 8 + V_h.numel() * 8
+
+    def step(raw, h, V):
+        s = sqd.build_strings(ctx, raw, w.norb, w.nelec_a)
+        t = sqd.excitation_tables(ctx, w.norb, s, w.nelec_a, s, w.nelec_b, h, V, 0.0)
+        e, C, it, res, rc = sqd.davidson(ctx, t, **opts)
+        t.close()
+        del C
+        return e, it, res
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step(raw_d, h_d, V_d)
+    barrier()
+    ctx.profile(True)
+    clk = ClockSampler(local_rank)
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    results = []
+    for _ in range(args.steps):
+        results.append(step(raw_d, h_d, V_d))
+    ev1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    dev_ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_read()
+    launches = ctx.launch_count()
+    hc = prof["same_spin_alpha"]["regions"]  # one region per sigma of one vector
+
+    # e2e: host buffers in, energies out, copies inside the timed region
+    ctx.profile(False)
+    n_e2e = args.e2e_steps if args.e2e_steps is not None else max(1, min(args.steps, 2))
+    barrier()
+    t0 = time.perf_counter()
+    e2e_s = 1.0
+    for _ in range(n_e2e):
+        raw_x = raw_h.to(dev, non_blocking=True)
+        hx = h_h.to(dev, non_blocking=True)
+        Vx = V_h.to(dev, non_blocking=True)
+        e, it, res = step(raw_x, hx, Vx)  # energies come back to the host
+    barrier()
+    if n_e2e:
+        e2e_s = time.perf_counter() - t0
+
+    # aggregate over ranks: total work / max time
+    t_max = dev_ms
+    hc_tot = hc
+    if world > 1:
+        tt = torch.tensor([dev_ms, e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max, e2e_max = float(tt[0]), float(tt[1])
+        cnt = torch.tensor([hc], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(cnt)
+        hc_tot = float(cnt[0])
+    else:
+        e2e_max = e2e_s
+    if rank != 0:
+        return None
+
+    per_step_hc = hc / args.steps
+    value = hc_tot / (t_max / 1e3)
+    e2e_value = per_step_hc * n_e2e * world / e2e_max if n_e2e else None
+
+    # roofline of the dominant sigma kernel (largest event time)
+    sig = {k: prof[k] for k in ("same_spin_alpha", "same_spin_beta", "alpha_beta")}
+    dom = max(sig, key=lambda k: sig[k]["ms"])
+    d = sig[dom]
+    achieved = (d["flops"] / d["regions"]) / (d["ms"] / d["regions"] / 1e3) / 1e12
+    kname = {"same_spin_alpha": "k_same_spin", "same_spin_beta": "k_same_spin",
+             "alpha_beta": "k_alpha_beta"}[dom]
+    roof = {"bound": "alu", "kernel": "%s (%s)" % (kname, dom),
+            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(dom),
+            "peak_source": "derived FP64: 152 SMs x 2070 MHz x 4 flop/clk/SM",
+            "launch_ms": d["ms"] / d["regions"], "flops_per_launch": d["flops"] / d["regions"]}
+    sigma_ms = sum(v["ms"] for v in sig.values()) + prof["transpose"]["ms"]
+    sigma_flops = sum(v["flops"] for v in sig.values())
+    res_last = results[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: seeded integrals and sampled strings shaped like the paper's "
+                "H2O/N2 sets (no dataset available)",
+        "config": {"workload": DESCR[args.workload],
+                   "l2": "inputs larger than L2 (3.2 GB vectors)" if w.ndet > 2e7 else
+                   "vectors may fit in L2",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "time_to_converged_E_s": t_max / 1e3 / args.steps,
+        "davidson_iterations": int(res_last[1]),
+        "energy": float(res_last[0][0]),
+        "sigma_per_step": per_step_hc,
+        "det_per_s": value * w.ndet,
+        "sigma_fp64_tflops": sigma_flops / (sigma_ms / 1e3) / 1e12,
+        "sigma_share_of_step": sigma_ms / dev_ms,
+        "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
+        "roofline": roof,
+        "hbm_roofline": {
+            "bound": "hbm", "note": "compulsory sigma bytes (read C, read/write sigma, "
+                                    "diagonal) / sigma time against measured copy bandwidth",
+            "achieved": sum(prof[k]["bytes"] for k in
+                            ("same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose"))
+            / (sigma_ms / 1e3) / 1e9 if sigma_ms else None,
+            "peak": _hbm_peak(), "unit": "GB/s"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "steps": n_e2e,
+                "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": 8 * opts["nroots"]},
+        "clocks": clocks,
+        "gpu_launches": launches,
+    }
+    line["hbm_roofline"]["frac"] = (line["hbm_roofline"]["achieved"] / line["hbm_roofline"]["peak"]
+                                    if line["hbm_roofline"]["achieved"] else None)
+    if n_e2e == 0:
+        line["e2e"] = None
+    ctx.close()
+    if args.sigma_extra != "none" and world == 1:
+        a2 = argparse.Namespace(**vars(args))
+        a2.workload, a2.steps, a2.warmup = args.sigma_extra, 3, 3
+        ex = run_sigma_only(a2, rank, world, local_rank)
+        line["sigma_only"] = {k: ex[k] for k in ("value", "unit", "ms_per_step", "kernels",
+                                                 "transpose_ms", "clocks")}
+        line["sigma_only"]["workload"] = DESCR[args.sigma_extra]
+        line["sigma_only"]["det_per_s"] = \
+            ex["value"] * ex["tables"]["n_alpha"] * ex["tables"]["n_beta"]
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_rows or default_cpu_rows(args.workload))
+    return line
+
+
+def run_sigma_only(args, rank, world, local_rank):
+    """One sigma = H C per step on tables built before the timed region."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2601_16169_gb300 as sqd
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = si.workload(args.workload)
+    ctx = sqd.Context(local_rank)
+    s = sqd.build_strings(ctx, torch.from_numpy(w.raw_a.view(np.int64).copy()).to(dev),
+                          w.norb, w.nelec_a)
+    t = sqd.excitation_tables(ctx, w.norb, s, w.nelec_a, s, w.nelec_b,
+                              torch.from_numpy(w.h).to(dev), torch.from_numpy(w.V).to(dev), 0.0)
+    C = torch.from_numpy(si.random_vectors(1, w.ndet, 13).reshape(
+        w.strings_a.size, w.strings_b.size)).to(dev)
+    S = torch.empty_like(C)
+    for _ in range(args.warmup):
+        sqd.sigma(ctx, t, C, S)
+    torch.cuda.synchronize(dev)
+    ctx.profile(True)
+    clk = ClockSampler(local_rank)
+    clk.start()
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sqd.sigma(ctx, t, C, S)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_read()
+    launches = ctx.launch_count()
+    if rank != 0:
+        return None
+    sig = {k: prof[k] for k in ("same_spin_alpha", "same_spin_beta", "alpha_beta")}
+    out = {"mode": "sigma", "metric": METRIC, "value": args.steps / (ms / 1e3), "unit": UNIT,
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "dtype": "f64",
+           "config": {"workload": DESCR[args.workload]}, "tables": t.info(),
+           "kernels": {k: dict(ms_per_launch=v["ms"] / max(1, v["regions"]),
+                               tflops=(v["flops"] / (v["ms"] / 1e3) / 1e12) if v["ms"] else 0.0,
+                               frac_fp64_peak=((v["flops"] / (v["ms"] / 1e3) / 1e12)
+                                               / FP64_PEAK_TFLOPS) if v["ms"] else 0.0)
+                       for k, v in sig.items()},
+           "transpose_ms": prof["transpose"]["ms"] / max(1, args.steps),
+           "clocks": clocks, "gpu_launches": launches}
+    t.close()
+    ctx.close()
+    return out
+
+
+def _hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
+# ------------------------------------------------------- reference -------
+
+def run_reference(args, rank, world):
+    """The oracle as it stands on the host cores: each step one bounded
+    sample of sigma rows of the same workload."""
+    if rank != 0:
+        return None
+    w = si.workload(args.workload)
+    rows_n = args.cpu_rows or max(1000, default_cpu_rows(args.workload) // 4)
+    for _ in range(args.warmup):
+        cpu_baseline(w, max(1000, rows_n // 10))
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = cpu_baseline(w, rows_n)
+        vals.append(r["value"])
+        secs.append(r["seconds"])
+    v = float(np.mean(vals))
+    cores = r["cores"]
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": DESCR[args.workload],
+                                            "parallelism": "host cores"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = _args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    elif args.mode == "sigma":
+        line = run_sigma_only(args, rank, world, local_rank)
+    else:
+        line = run_ours(args, rank, world, local_rank)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -186,7 +186,9 @@ typedef struct {
  * the nroots vectors in d_C if use_guess.  Correction t = r / (theta -
  * H_II) with |denominator| clamped to precond_floor; classical Gram-Schmidt
  * twice, a vector is dropped if its norm after that is below 1e-12; at the
- * subspace limit the basis restarts from the 2*nroots lowest Ritz vectors;
+ * subspace limit the basis restarts from the 2*nroots lowest Ritz vectors
+ * plus the nroots Ritz vectors of the previous iteration orthonormalised
+ * against them (GD+k restart; max_subspace must be >= 4*nroots);
  * converged when every root has ||r|| <= tol_residual and
  * |delta theta| <= tol_energy.  Rayleigh-Ritz uses a one-block Jacobi
  * eigensolver in FP64.
@@ -215,6 +217,17 @@ int sqd_davidson(sqd_ctx *ctx, sqd_tables *tables, const sqd_options *opt,
  */
 int sqd_rdm(sqd_ctx *ctx, sqd_tables *tables, const double *d_C,
             double *d_rdm1, double *d_rdm2);
+
+/*
+ * Orbital-rotation gradient of E for orbitals rotated by U = exp(kappa),
+ * kappa antisymmetric, h' = U^T h U, V rotated on all four indices:
+ * d_grad[p*norb+q] = dE/dkappa_pq at kappa = 0 = 2 (F_pq - F_qp) with the
+ * generalized Fock matrix F_pq = sum_r h_pr rdm1_qr + sum_rst (pr|st)
+ * rdm2_qrst (device buffers; rdm1, rdm2 as written by sqd_rdm, for the
+ * integrals of `tables`).  Not in the paper.
+ */
+int sqd_orbital_gradient(sqd_ctx *ctx, sqd_tables *tables, const double *d_rdm1,
+                         const double *d_rdm2, double *d_grad);
 
 /* ------------------------------------------------------ measurement --- */
 

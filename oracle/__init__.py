@@ -304,7 +304,10 @@ def davidson(matvec, hdiag, nroots=1, tol_residual=1e-8, tol_energy=1e-8,
     * classical Gram-Schmidt applied twice; a vector whose norm after the
       two passes is below ``drop_tol`` is dropped;
     * subspace limit max(8 * nroots, 16); on reaching it, restart from the
-      2 * nroots lowest Ritz vectors;
+      2 * nroots lowest Ritz vectors plus the nroots Ritz vectors of the
+      previous iteration, orthonormalised against them (the GD+k restart of
+      Stathopoulos and Saad, 1998); a previous direction whose norm after
+      two Gram-Schmidt passes is below 1e-8 is left out;
     * converged when every root has ||r||_2 <= tol_residual and
       |theta - theta_previous| <= tol_energy.
     Returns (theta, X, iterations, residual_norms, converged).
@@ -324,6 +327,7 @@ def davidson(matvec, hdiag, nroots=1, tol_residual=1e-8, tol_energy=1e-8,
     theta_old = np.full(nroots, np.inf)
     it = 0
     converged = False
+    Yprev = None  # previous Ritz coefficients, in the basis of that iteration
     while True:
         G = Vb.T @ Wb
         G = 0.5 * (G + G.T)
@@ -349,8 +353,26 @@ def davidson(matvec, hdiag, nroots=1, tol_residual=1e-8, tol_energy=1e-8,
         nkeep = Vb.shape[1]
         if nkeep + len(T) > max_subspace:
             m = min(2 * nroots, Vb.shape[1])
-            Vb = Vb @ Y[:, :m]
-            Wb = Wb @ Y[:, :m]
+            Z = Y[:, :m]
+            if Yprev is not None:
+                cols = []
+                for j in range(Yprev.shape[1]):
+                    p = np.zeros(Vb.shape[1])
+                    p[:Yprev.shape[0]] = Yprev[:, j]
+                    for _ in range(2):
+                        p = p - Z @ (Z.T @ p)
+                        for c in cols:
+                            p = p - c * (c @ p)
+                    nrm = np.linalg.norm(p)
+                    if nrm > 1e-8:
+                        cols.append(p / nrm)
+                if cols:
+                    Z = np.concatenate([Z, np.stack(cols, axis=1)], axis=1)
+            Vb = Vb @ Z
+            Wb = Wb @ Z
+            Yprev = np.eye(Z.shape[1])[:, :nroots]
+        else:
+            Yprev = Y[:, :nroots].copy()
         new = []
         for t in T:
             for _ in range(2):

@@ -24,6 +24,7 @@ import torch
 __all__ = [
     "SQDError", "lib", "library_path", "Context", "Tables", "Options",
     "build_strings", "excitation_tables", "sigma", "davidson", "diagonal", "rdm",
+    "orbital_gradient", "SQDEnergy",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -43,7 +44,7 @@ EXPORTED = [
     "sqd_create", "sqd_set_stream", "sqd_destroy", "sqd_last_error", "sqd_version",
     "sqd_build_strings", "sqd_excitation_tables", "sqd_free_tables", "sqd_tables_info",
     "sqd_tables_export", "sqd_diagonal", "sqd_sigma", "sqd_davidson", "sqd_rdm",
-    "sqd_profile_enable", "sqd_profile_read", "sqd_launch_count",
+    "sqd_profile_enable", "sqd_profile_read", "sqd_launch_count", "sqd_orbital_gradient",
 ]
 
 PROFILE_CLASSES = ["same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose", "tables",
@@ -103,6 +104,7 @@ def lib():
                                    ctypes.POINTER(i64), ctypes.POINTER(dbl),
                                    ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     L.sqd_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
+    L.sqd_orbital_gradient.argtypes = [vp, vp, vp, vp, vp]
     _LIB = L
     return L
 
@@ -319,3 +321,44 @@ def rdm(ctx: Context, tables: Tables, C: torch.Tensor, two_body: bool = True):
     g2 = torch.empty((n, n, n, n), dtype=torch.float64, device=dev) if two_body else None
     ctx._check(ctx._lib.sqd_rdm(ctx.handle, tables.handle, _ptr(C), _ptr(g1), _ptr(g2)))
     return g1, g2
+
+
+def orbital_gradient(ctx: Context, tables: Tables, g1: torch.Tensor,
+                     g2: torch.Tensor) -> torch.Tensor:
+    """sqd_orbital_gradient: dE/dkappa_pq = 2 (F_pq - F_qp) from the RDMs."""
+    _need_cuda(g1, "rdm1", torch.float64)
+    _need_cuda(g2, "rdm2", torch.float64)
+    g = torch.empty_like(g1)
+    ctx._check(ctx._lib.sqd_orbital_gradient(ctx.handle, tables.handle, _ptr(g1), _ptr(g2),
+                                             _ptr(g)))
+    return g
+
+
+class SQDEnergy(torch.autograd.Function):
+    """E(h, V) = lowest eigenvalue of P H P on the given string sets, with
+    the Hellmann-Feynman backward dE/dh = rdm1, dE/dV = rdm2 / 2 (C is an
+    exact eigenvector of P H P and P does not depend on the integrals).
+    Only the converged state C is kept for backward, no Davidson history.
+
+    Usage: E = SQDEnergy.apply(h, V, ctx, alpha, nalpha_e, beta, nbeta_e,
+    ecore, tol_residual)."""
+
+    @staticmethod
+    def forward(fctx, h, V, ctx, alpha, nalpha_e, beta, nbeta_e, ecore=0.0,
+                tol_residual=1e-9):
+        norb = h.shape[0]
+        t = excitation_tables(ctx, norb, alpha, nalpha_e, beta, nbeta_e,
+                              h.detach().contiguous(), V.detach().contiguous(), ecore)
+        e, C, it, res, rc = davidson(ctx, t, nroots=1, tol_residual=tol_residual,
+                                     tol_energy=1e-12, max_iter=500)
+        fctx.sqd = (ctx, t)
+        fctx.save_for_backward(C)
+        return torch.tensor(e[0], dtype=torch.float64, device=h.device)
+
+    @staticmethod
+    def backward(fctx, grad):
+        (C,) = fctx.saved_tensors
+        ctx, t = fctx.sqd
+        g1, g2 = rdm(ctx, t, C[0].contiguous())
+        t.close()
+        return (grad * g1, 0.5 * grad * g2, None, None, None, None, None, None, None)

@@ -412,8 +412,9 @@ void sqd_free_tables(sqd_tables *t) {
     cudaDeviceSynchronize();
     free_spin(&t->a);
     if (!t->shared) free_spin(&t->b_own);
-    void *ptrs[] = {t->h, t->V, t->diag, t->ab.chunk_rows, t->ab.group_rows, t->scratch_t,
-                    t->scratch_s};
+    void *ptrs[] = {t->h,         t->V,          t->diag,       t->ab.chunk_rows,
+                    t->ab.group_rows, t->scratch_t, t->scratch_s, t->rdm_iket,
+                    t->rdm_ibra,  t->rdm_ipq,    t->rdm_chunks, t->rdm_groups};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete t;
@@ -555,10 +556,11 @@ int sqd_sigma(sqd_ctx *ctx, sqd_tables *t, const double *d_C, double *d_sigma, i
 struct dav_work {
     double *Vb = nullptr, *Wb = nullptr, *X = nullptr, *R = nullptr, *Tmp = nullptr;
     double *G = nullptr, *evals = nullptr, *evecs = nullptr, *dots = nullptr, *partial = nullptr;
-    double *phase = nullptr;
+    double *phase = nullptr, *Yprev = nullptr, *Z = nullptr;
     int64_t *idx = nullptr;
+    int *rdev = nullptr;
     ~dav_work() {
-        void *p[] = {Vb, Wb, X, R, Tmp, G, evals, evecs, dots, partial, phase, idx};
+        void *p[] = {Vb, Wb, X, R, Tmp, G, evals, evecs, dots, partial, phase, idx, Yprev, Z, rdev};
         for (void *q : p)
             if (q) cudaFree(q);
     }
@@ -572,16 +574,20 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
     int M = o->max_subspace > 0 ? o->max_subspace : std::max(8 * k, 16);
     if (M > 112) M = 112;
     if ((int64_t)M > N) M = (int)N;
-    if (M < std::min<int64_t>(3 * k, N))
-        return sqd_fail(ctx, SQD_EINVAL, "max_subspace must be >= 3*nroots (or the dimension)");
+    if (M < std::min<int64_t>(4 * k, N))
+        return sqd_fail(ctx, SQD_EINVAL, "max_subspace must be >= 4*nroots (or the dimension)");
     const int nblk = multidot_blocks(N);
     const int k2 = std::min(2 * k, M);
+    const int kr = std::min(3 * k, M);  // restart basis: 2k Ritz + k previous Ritz
     dav_work w;
     SQD_TRY(dalloc(ctx, &w.Vb, (int64_t)M * N));
     SQD_TRY(dalloc(ctx, &w.Wb, (int64_t)M * N));
     SQD_TRY(dalloc(ctx, &w.X, (int64_t)k * N));
     SQD_TRY(dalloc(ctx, &w.R, (int64_t)k * N));
-    SQD_TRY(dalloc(ctx, &w.Tmp, (int64_t)k2 * N));
+    SQD_TRY(dalloc(ctx, &w.Tmp, (int64_t)kr * N));
+    SQD_TRY(dalloc(ctx, &w.Yprev, (int64_t)M * k));
+    SQD_TRY(dalloc(ctx, &w.Z, (int64_t)M * kr));
+    SQD_TRY(dalloc(ctx, &w.rdev, 1));
     SQD_TRY(dalloc(ctx, &w.G, (int64_t)M * M));
     SQD_TRY(dalloc(ctx, &w.evals, M));
     SQD_TRY(dalloc(ctx, &w.evecs, (int64_t)M * M));
@@ -633,6 +639,7 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
 
     std::vector<double> theta(M), theta_old(k, INFINITY), rn2(k), rn(k);
     int it = 0;
+    int mprev = 0;  // rows of Yprev (0: no previous Ritz vectors yet)
     int status = SQD_OK;
     for (;;) {
         SQD_TRY(launch_jacobi_eigh(ctx, w.G, M, m, w.evals, w.evecs));
@@ -665,16 +672,30 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
         it++;
         for (int j = 0; j < k; j++) theta_old[j] = theta[j];
         if (m + (int)todo.size() > M) {
-            // thick restart on the 2k lowest Ritz vectors
+            // restart (GD+k): the 2k lowest Ritz vectors plus the k Ritz vectors
+            // of the previous iteration, orthonormalised against them
             int m2 = std::min(k2, m);
-            SQD_TRY(launch_combine(ctx, w.Vb, N, m, w.evecs, m, m2, w.Tmp, N, N));
-            SQD_CUDA(ctx, cudaMemcpyAsync(w.Vb, w.Tmp, sizeof(double) * m2 * N,
+            SQD_TRY(launch_gdk_basis(ctx, w.evecs, m, m2, mprev ? w.Yprev : nullptr, mprev, k, M,
+                                     w.Z, M, w.rdev));
+            int r = m2;
+            SQD_CUDA(ctx, cudaMemcpyAsync(&r, w.rdev, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SQD_CUDA(ctx, cudaStreamSynchronize(st));
+            SQD_TRY(launch_combine(ctx, w.Vb, N, m, w.Z, M, r, w.Tmp, N, N));
+            SQD_CUDA(ctx, cudaMemcpyAsync(w.Vb, w.Tmp, sizeof(double) * r * N,
                                           cudaMemcpyDeviceToDevice, st));
-            SQD_TRY(launch_combine(ctx, w.Wb, N, m, w.evecs, m, m2, w.Tmp, N, N));
-            SQD_CUDA(ctx, cudaMemcpyAsync(w.Wb, w.Tmp, sizeof(double) * m2 * N,
+            SQD_TRY(launch_combine(ctx, w.Wb, N, m, w.Z, M, r, w.Tmp, N, N));
+            SQD_CUDA(ctx, cudaMemcpyAsync(w.Wb, w.Tmp, sizeof(double) * r * N,
                                           cudaMemcpyDeviceToDevice, st));
-            m = m2;
+            m = r;
             for (int j = 0; j < m; j++) SQD_TRY(dot_col(j + 1, j));
+            // the current Ritz vectors are the first k basis vectors now
+            SQD_TRY(launch_identity_cols(ctx, w.Yprev, m, k, M));
+            mprev = m;
+        } else {
+            SQD_CUDA(ctx, cudaMemcpy2DAsync(w.Yprev, sizeof(double) * M, w.evecs,
+                                            sizeof(double) * m, sizeof(double) * m, k,
+                                            cudaMemcpyDeviceToDevice, st));
+            mprev = m;
         }
         int m_old = m;
         for (int j : todo) {
@@ -734,6 +755,14 @@ int sqd_rdm(sqd_ctx *ctx, sqd_tables *t, const double *d_C, double *d_rdm1, doub
     if (!d_C || !d_rdm1) return sqd_fail(ctx, SQD_EINVAL, "NULL buffer");
     SQD_TRY(use_device(ctx));
     return launch_rdm(ctx, t, d_C, d_rdm1, d_rdm2);
+}
+
+int sqd_orbital_gradient(sqd_ctx *ctx, sqd_tables *t, const double *d_rdm1,
+                         const double *d_rdm2, double *d_grad) {
+    if (!ctx || !t) return fail_noctx(SQD_EINVAL, "sqd_orbital_gradient: NULL argument");
+    if (!d_rdm1 || !d_rdm2 || !d_grad) return sqd_fail(ctx, SQD_EINVAL, "NULL buffer");
+    SQD_TRY(use_device(ctx));
+    return launch_orbital_gradient(ctx, t, d_rdm1, d_rdm2, d_grad);
 }
 
 }  // extern "C"

@@ -416,6 +416,72 @@ int launch_set_unit(sqd_ctx *ctx, double *V, int64_t ld, int k, const int64_t *i
     return SQD_OK;
 }
 
+// ------------------------------------------------------- GD+k restart ---
+// Z[:, 0..m2) = Y[:, 0..m2) (the lowest Ritz coefficients), then each of the
+// k previous Ritz coefficient columns P[:, j] (rows >= mp are zero) is
+// orthogonalised twice against the columns of Z so far and appended if its
+// norm stays above 1e-8.  One block; m <= 112.  *r_out = columns of Z.
+__global__ void __launch_bounds__(128) k_gdk_basis(const double *__restrict__ Y, int m, int m2,
+                                                   const double *__restrict__ P, int mp, int k,
+                                                   int ldp, double *__restrict__ Z, int ldz,
+                                                   int *__restrict__ r_out) {
+    __shared__ double p[JAC_MAX];
+    __shared__ double red[32];
+    __shared__ double coef;
+    const int i = threadIdx.x;
+    for (int j = 0; j < m2; j++)
+        if (i < m) Z[i + (int64_t)j * ldz] = Y[i + (int64_t)j * m];
+    __syncthreads();
+    int r = m2;
+    for (int j = 0; j < k; j++) {
+        if (i < m) p[i] = (i < mp && P) ? P[i + (int64_t)j * ldp] : 0.0;
+        __syncthreads();
+        for (int pass = 0; pass < 2; pass++) {
+            for (int c = 0; c < r; c++) {
+                double v = (i < m) ? Z[i + (int64_t)c * ldz] * p[i] : 0.0;
+                double d = block_sum(v, red);
+                if (i == 0) coef = d;
+                __syncthreads();
+                if (i < m) p[i] -= coef * Z[i + (int64_t)c * ldz];
+                __syncthreads();
+            }
+        }
+        double nv = (i < m) ? p[i] * p[i] : 0.0;
+        double n2 = block_sum(nv, red);
+        if (i == 0) coef = n2;
+        __syncthreads();
+        double nrm = sqrt(coef);
+        if (nrm > 1e-8) {  // uniform across the block
+            if (i < m) Z[i + (int64_t)r * ldz] = p[i] / nrm;
+            r++;
+        }
+        __syncthreads();
+    }
+    if (i == 0) *r_out = r;
+}
+
+int launch_gdk_basis(sqd_ctx *ctx, const double *Y, int m, int m2, const double *P, int mp,
+                     int k, int ldp, double *Z, int ldz, int *r_dev) {
+    if (m > JAC_MAX) return sqd_fail(ctx, SQD_EINVAL, "subspace too large");
+    k_gdk_basis<<<1, 128, 0, ctx->stream>>>(Y, m, m2, P, mp, k, ldp, Z, ldz, r_dev);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// Yprev = first k columns of the identity (r rows, leading dimension ld)
+__global__ void k_identity_cols(double *Y, int r, int k, int ld) {
+    for (int t = threadIdx.x; t < r * k; t += blockDim.x) {
+        int i = t % r, j = t / r;
+        Y[i + (int64_t)j * ld] = (i == j) ? 1.0 : 0.0;
+    }
+}
+
+int launch_identity_cols(sqd_ctx *ctx, double *Y, int r, int k, int ld) {
+    k_identity_cols<<<1, 256, 0, ctx->stream>>>(Y, r, k, ld);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
 // ---------------------------------------------------------------- phase --
 // Flip each vector so that its largest-magnitude component (lowest index on
 // ties) is positive.

@@ -93,7 +93,39 @@ int launch_same_spin(sqd_ctx *ctx, const spin_tables *R, const spin_tables *Cc, 
 #define AB_YW 256                          // beta rows (slab width) per block
 #define AB_NA 16                           // alpha singles staged per batch
 
-__global__ void __launch_bounds__(AB_THREADS)
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Work items of a block are (alpha row, batch of AB_NA alpha singles) pairs
+// over the rows of its group that have singles, in order.  The slabs of
+// item i+1 are copied (cp.async) while item i is computed.
+struct ab_item {
+    int64_t ia, ab, a1;  // row, first single of the batch, end of the row's singles
+};
+
+__device__ __forceinline__ bool ab_next(const int64_t *__restrict__ a_off, int64_t g1,
+                                        ab_item &it) {
+    it.ab += AB_NA;
+    if (it.ab < it.a1) return true;
+    for (int64_t ia = it.ia + 1; ia < g1; ia++) {
+        int64_t a0 = a_off[ia], a1 = a_off[ia + 1];
+        if (a1 > a0) {
+            it.ia = ia;
+            it.ab = a0;
+            it.a1 = a1;
+            return true;
+        }
+    }
+    it.ia = g1;
+    return false;
+}
+
+__global__ void __launch_bounds__(AB_THREADS, 2)
     k_alpha_beta(int64_t nb, int norb2, const int64_t *__restrict__ a_off,
                  const int32_t *__restrict__ a_tgt, const uint16_t *__restrict__ a_pq,
                  const int8_t *__restrict__ a_sgn, const int64_t *__restrict__ b_off,
@@ -101,9 +133,11 @@ __global__ void __launch_bounds__(AB_THREADS)
                  const int8_t *__restrict__ b_sgn, const int64_t *__restrict__ chunk_rows,
                  const int64_t *__restrict__ group_rows, const double *__restrict__ C,
                  double *__restrict__ S, const double *__restrict__ V) {
-    __shared__ double slab[AB_NA][AB_YW];
-    __shared__ int64_t sh_vrow[AB_NA];
-    __shared__ uint32_t sh_sa[AB_NA];
+    // double-buffered slabs in dynamic shared memory: [2][AB_NA][AB_YW] doubles
+    extern __shared__ double ab_dyn[];
+    double(*slab)[AB_NA][AB_YW] = reinterpret_cast<double(*)[AB_NA][AB_YW]>(ab_dyn);
+    __shared__ int64_t sh_vrow[2][AB_NA];
+    __shared__ uint32_t sh_sa[2][AB_NA];
     __shared__ int64_t sh_off[AB_YW + 1];
 
     const int tid = threadIdx.x;
@@ -113,76 +147,94 @@ __global__ void __launch_bounds__(AB_THREADS)
     __syncthreads();
     const int64_t e0 = sh_off[0], e1 = sh_off[width];
 
-    // this thread's beta entries: target Ib, V column index, sign bit, slab column
+    // this thread's beta entries: neighbour Ib and packed
+    // (V column | slab column << 12 | sign << 31)
     int32_t ib[AB_EPT];
-    int32_t vcol[AB_EPT];
-    int32_t jloc[AB_EPT];
-    uint32_t sb[AB_EPT];
+    uint32_t info[AB_EPT];
     double acc[AB_EPT];
 #pragma unroll
     for (int k = 0; k < AB_EPT; k++) {
         int64_t e = e0 + tid + (int64_t)k * AB_THREADS;
+        ib[k] = -1;
+        info[k] = 0;
         if (e < e1) {
-            ib[k] = b_tgt[e];
-            vcol[k] = b_pq[e];
-            sb[k] = (b_sgn[e] < 0) ? 1u : 0u;
-            // slab column: the beta row of entry e (upper bound search)
             int lo = 0, hi = width;  // sh_off[lo] <= e < sh_off[hi]
             while (hi - lo > 1) {
                 int mid = (lo + hi) >> 1;
                 if (sh_off[mid] <= e) lo = mid; else hi = mid;
             }
-            jloc[k] = lo;
-        } else {
-            ib[k] = -1;
-            vcol[k] = 0;
-            sb[k] = 0;
-            jloc[k] = 0;
+            ib[k] = b_tgt[e];
+            info[k] = (uint32_t)b_pq[e] | ((uint32_t)lo << 12) | ((b_sgn[e] < 0) ? 0x80000000u : 0u);
         }
+        acc[k] = 0.0;
     }
 
     const int64_t g0 = group_rows[blockIdx.y], g1 = group_rows[blockIdx.y + 1];
-    for (int64_t ia = g0; ia < g1; ia++) {
-        const int64_t a0 = a_off[ia], a1 = a_off[ia + 1];
-        if (a0 == a1) continue;
+    // stage the slabs and alpha data of one item into buffer `buf`
+    auto stage = [&](const ab_item &it, int buf) {
+        const int nbat = (int)min((int64_t)AB_NA, it.a1 - it.ab);
+        if (tid < nbat) {
+            sh_vrow[buf][tid] = (int64_t)a_pq[it.ab + tid] * norb2;
+            sh_sa[buf][tid] = (a_sgn[it.ab + tid] < 0) ? 1u : 0u;
+        }
+        for (int idx = tid; idx < nbat * width; idx += AB_THREADS) {
+            int a = idx / width, j = idx - a * width;
+            cp_async8(&slab[buf][a][j], C + (int64_t)a_tgt[it.ab + a] * nb + y0 + j);
+        }
+        cp_async_commit();
+    };
+
+    ab_item cur;
+    cur.ia = g0 - 1;
+    cur.ab = 0;
+    cur.a1 = 0;
+    bool have = ab_next(a_off, g1, cur);
+    if (have) stage(cur, 0);
+    int buf = 0;
+    while (have) {
+        ab_item nxt = cur;
+        bool more = ab_next(a_off, g1, nxt);
+        if (more) stage(nxt, buf ^ 1);
+        else cp_async_commit();  // keep the group count uniform
+        cp_async_wait<1>();
+        __syncthreads();  // slabs of `cur` visible to all threads
+        const int nbat = (int)min((int64_t)AB_NA, cur.a1 - cur.ab);
+        for (int a = 0; a < nbat; a++) {
+            const double *vr = V + sh_vrow[buf][a];
+            const uint32_t sa = sh_sa[buf][a] << 31;
+            const double *sl = slab[buf][a];
 #pragma unroll
-        for (int k = 0; k < AB_EPT; k++) acc[k] = 0.0;
-        for (int64_t ab = a0; ab < a1; ab += AB_NA) {
-            const int nbat = (int)min((int64_t)AB_NA, a1 - ab);
-            __syncthreads();  // previous batch fully consumed
-            if (tid < nbat) {
-                sh_vrow[tid] = (int64_t)a_pq[ab + tid] * norb2;
-                sh_sa[tid] = (a_sgn[ab + tid] < 0) ? 1u : 0u;
-            }
-            for (int idx = tid; idx < nbat * width; idx += AB_THREADS) {
-                int a = idx / width, j = idx - a * width;
-                slab[a][j] = C[(int64_t)a_tgt[ab + a] * nb + y0 + j];
-            }
-            __syncthreads();
-            for (int a = 0; a < nbat; a++) {
-                const double *vr = V + sh_vrow[a];
-                const uint32_t sa = sh_sa[a];
-#pragma unroll
-                for (int k = 0; k < AB_EPT; k++) {
-                    double v = __ldg(vr + vcol[k]);
-                    unsigned long long bits =
-                        (unsigned long long)__double_as_longlong(v) ^
-                        ((unsigned long long)(sa ^ sb[k]) << 63);
-                    acc[k] = fma(__longlong_as_double((long long)bits), slab[a][jloc[k]], acc[k]);
-                }
+            for (int k = 0; k < AB_EPT; k++) {
+                const uint32_t inf = info[k];
+                double v = __ldg(vr + (inf & 0xfffu));
+                unsigned long long bits = (unsigned long long)__double_as_longlong(v) ^
+                                          ((unsigned long long)((inf ^ sa) & 0x80000000u) << 32);
+                acc[k] = fma(__longlong_as_double((long long)bits), sl[(inf >> 12) & 0x1ffu], acc[k]);
             }
         }
+        if (cur.ab + AB_NA >= cur.a1) {  // last batch of this alpha row: flush
 #pragma unroll
-        for (int k = 0; k < AB_EPT; k++)
-            if (ib[k] >= 0) atomicAdd(&S[ia * nb + ib[k]], acc[k]);
+            for (int k = 0; k < AB_EPT; k++) {
+                if (ib[k] >= 0) atomicAdd(&S[cur.ia * nb + ib[k]], acc[k]);
+                acc[k] = 0.0;
+            }
+        }
+        __syncthreads();  // buffer `buf` is reused by the item after next
+        cur = nxt;
+        have = more;
+        buf ^= 1;
     }
+    cp_async_wait<0>();
 }
 
 int launch_alpha_beta(sqd_ctx *ctx, const sqd_tables *t, const double *C, double *S) {
     const spin_tables *A = &t->a, *B = t->b;
     if (A->nnz1 == 0 || B->nnz1 == 0) return SQD_OK;
     dim3 g((unsigned)t->ab.nchunks, (unsigned)t->ab.ngroups);
-    k_alpha_beta<<<g, AB_THREADS, 0, ctx->stream>>>(
+    const size_t shm = sizeof(double) * 2 * AB_NA * AB_YW;
+    SQD_CUDA(ctx, cudaFuncSetAttribute(k_alpha_beta, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)shm));
+    k_alpha_beta<<<g, AB_THREADS, shm, ctx->stream>>>(
         B->n, t->norb * t->norb, A->off1, A->tgt1, A->pq1, A->sgn1, B->off1, B->tgt1, B->pq1,
         B->sgn1, t->ab.chunk_rows, t->ab.group_rows, C, S, t->V);
     SQD_LAUNCHED(ctx);

@@ -103,6 +103,13 @@ struct sqd_tables {
     // sigma scratch
     double *scratch_t = nullptr;  // C^T
     double *scratch_s = nullptr;  // (sigma_bb)^T
+    // RDM: extended alpha items sorted by pq, beta chunks, item groups
+    bool rdm_ready = false;
+    int64_t rdm_items = 0;
+    int32_t *rdm_iket = nullptr, *rdm_ibra = nullptr;
+    uint32_t *rdm_ipq = nullptr;
+    int rdm_nchunks = 0, rdm_ngroups = 0;
+    int64_t *rdm_chunks = nullptr, *rdm_groups = nullptr;
     int64_t bytes = 0;
 };
 
@@ -193,6 +200,11 @@ int launch_jacobi_eigh(sqd_ctx *, const double *G, int ldg, int m, double *evals
 int launch_argmin_k(sqd_ctx *, const double *d, int64_t n, int k, int64_t *idx_dev);
 int launch_set_unit(sqd_ctx *, double *V, int64_t ld, int k, const int64_t *idx_dev);
 int launch_fix_phase(sqd_ctx *, double *X, int64_t ld, int k, int64_t n, double *work_dev);
+int launch_gdk_basis(sqd_ctx *, const double *Y, int m, int m2, const double *P, int mp, int k,
+                     int ldp, double *Z, int ldz, int *r_dev);
+int launch_identity_cols(sqd_ctx *, double *Y, int r, int k, int ld);
 
 // rdm
 int launch_rdm(sqd_ctx *, const sqd_tables *t, const double *C, double *rdm1, double *rdm2);
+int launch_orbital_gradient(sqd_ctx *, const sqd_tables *t, const double *g1, const double *g2,
+                            double *grad);
