@@ -186,7 +186,7 @@ def test_autograd_function(sqd, ctx):
     t = tables(sqd, ctx, w.norb, w.strings_a, 5, w.strings_a, 5, w.h, w.V)
     e, C, it, res, rc = sqd.davidson(ctx, t, nroots=1, tol_residual=1e-9, tol_energy=1e-12)
     g1, g2 = sqd.rdm(ctx, t, C[0].contiguous())
-    assert abs(float(E) - e[0]) <= 1e-9
+    assert abs(float(E.detach()) - e[0]) <= 1e-9
     assert torch.allclose(h.grad, g1, atol=1e-8)
     assert torch.allclose(V.grad, 0.5 * g2, atol=1e-8)
     t.close()
@@ -198,7 +198,9 @@ def test_adjoint29_finite_differences_20_entries(sqd, ctx):
     # (symmetry orbits moved together) against the RDMs
     w = si.workload("adjoint29")
     norb, sa = w.norb, w.strings_a
-    e0, C, t = _energy(sqd, ctx, norb, sa, 5, sa, 5, w.h, w.V, tol=1e-9)
+    # ||r|| <= 1e-8 keeps the RDM error near 1e-8; the perturbed energies need
+    # only ||r|| <= 1e-7 (energy error ~ ||r||^2 / gap, far below 1e-12)
+    e0, C, t = _energy(sqd, ctx, norb, sa, 5, sa, 5, w.h, w.V, tol=1e-8)
     g1, g2 = sqd.rdm(ctx, t, C[0].contiguous())
     g1, g2 = g1.cpu().numpy(), g2.cpu().numpy()
     t.close()
@@ -224,9 +226,9 @@ def test_adjoint29_finite_differences_20_entries(sqd, ctx):
             an = 0.5 * sum(g2[o] for o in orbit)
             args = lambda s_: (w.h, w.V + s_ * D)
         # warm start from the unperturbed ground state
-        ep, _, tp = _energy(sqd, ctx, norb, sa, 5, sa, 5, *args(step), tol=1e-9, guess=C)
+        ep, _, tp = _energy(sqd, ctx, norb, sa, 5, sa, 5, *args(step), tol=1e-7, guess=C)
         tp.close()
-        em, _, tm = _energy(sqd, ctx, norb, sa, 5, sa, 5, *args(-step), tol=1e-9, guess=C)
+        em, _, tm = _energy(sqd, ctx, norb, sa, 5, sa, 5, *args(-step), tol=1e-7, guess=C)
         tm.close()
         fd = (ep - em) / (2 * step)
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (i, fd, an)
