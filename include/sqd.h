@@ -91,6 +91,30 @@ const char *sqd_version(void);
 int sqd_build_strings(sqd_ctx *ctx, const uint64_t *d_raw, int64_t n_raw,
                       int norb, int nelec, uint64_t *d_out, int64_t *n_out);
 
+/*
+ * sqd_build_strings_noalloc: the same filter as sqd_build_strings, for
+ * callers that cannot allocate device memory -- for example a process whose
+ * device memory is all reserved by another allocator (a framework's caching
+ * allocator sized to the whole card), or a latency-critical loop that must
+ * not pay the device-wide synchronisation that cudaMalloc/cudaFree imply.
+ * The paper has no counterpart; it is an interface convenience.
+ *
+ * It allocates nothing: its scratch is a fixed 6.3 MB array in the
+ * library's device memory, which every GPU that loads the library holds
+ * until the process exits.  The caller passes the inputs and outputs exactly
+ * as for sqd_build_strings, with the same result.
+ *  - n_raw may be at most 262144 (2^18); larger inputs return SQD_EINVAL
+ *    (use sqd_build_strings).
+ *  - The first call on a device looks up the array's device address on that
+ *    device (cudaGetSymbolAddress); make that first call before any stream
+ *    capture.
+ *  - Every call shares the one array and leaves its contents behind: calls
+ *    that overlap on the GPU (from several streams, threads or contexts) race
+ *    and must be serialised by the caller.
+ */
+int sqd_build_strings_noalloc(sqd_ctx *ctx, const uint64_t *d_raw, int64_t n_raw,
+                              int norb, int nelec, uint64_t *d_out, int64_t *n_out);
+
 /* ---------------------------------- a2-a4: excitation tables, diagonal -- */
 
 /*

@@ -45,6 +45,7 @@ EXPORTED = [
     "sqd_build_strings", "sqd_excitation_tables", "sqd_free_tables", "sqd_tables_info",
     "sqd_tables_export", "sqd_diagonal", "sqd_sigma", "sqd_davidson", "sqd_rdm",
     "sqd_profile_enable", "sqd_profile_read", "sqd_launch_count", "sqd_orbital_gradient",
+    "sqd_build_strings_noalloc",
 ]
 
 PROFILE_CLASSES = ["same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose", "tables",
@@ -105,6 +106,7 @@ def lib():
                                    ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     L.sqd_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
     L.sqd_orbital_gradient.argtypes = [vp, vp, vp, vp, vp]
+    L.sqd_build_strings_noalloc.argtypes = [vp, vp, i64, i32, i32, vp, ctypes.POINTER(i64)]
     _LIB = L
     return L
 
@@ -242,6 +244,23 @@ def build_strings(ctx: Context, raw: torch.Tensor, norb: int, nelec: int) -> tor
     ctx._check(ctx._lib.sqd_build_strings(ctx.handle, _ptr(raw), raw.numel(), norb, nelec,
                                           _ptr(out), ctypes.byref(n)))
     return out[:n.value]
+
+
+def build_strings_noalloc(ctx: Context, raw: torch.Tensor, norb: int, nelec: int,
+                          out: torch.Tensor) -> int:
+    """sqd_build_strings_noalloc: the filter of build_strings for callers
+    that cannot allocate device memory (the library uses a fixed scratch
+    array instead).  ``out`` (caller-allocated, at least raw.numel() int64
+    elements) receives the strings; returns their count.  At most 2**18 raw
+    strings; calls that overlap on the GPU race on the shared scratch."""
+    _need_cuda(raw, "raw", torch.int64)
+    _need_cuda(out, "out", torch.int64)
+    if out.numel() < raw.numel():
+        raise ValueError("out is smaller than raw")
+    n = ctypes.c_int64(0)
+    ctx._check(ctx._lib.sqd_build_strings_noalloc(ctx.handle, _ptr(raw), raw.numel(), norb,
+                                                  nelec, _ptr(out), ctypes.byref(n)))
+    return n.value
 
 
 def excitation_tables(ctx: Context, norb: int, alpha: torch.Tensor, nalpha_e: int,
