@@ -228,6 +228,32 @@ int sqd_davidson(sqd_ctx *ctx, sqd_tables *tables, const sqd_options *opt,
                  double *h_energies, double *d_C, int *h_iters,
                  double *h_residuals);
 
+/* -------------------------------------------- batched subspaces ----- */
+
+/*
+ * Ground states of nbatch independent subspaces at once (SQD produces many
+ * subsampled configuration sets per round, Section I; each is one table
+ * object from sqd_excitation_tables, all on this context's device).
+ * Same Davidson readings as sqd_davidson with nroots == 1 (required),
+ * max_subspace 0 meaning 16.  Every step runs as one launch over all
+ * subspaces; one iteration is captured in a CUDA graph and replayed until
+ * every subspace has converged or stopped.  The number of alpha-row groups
+ * of the paired-singles work per subspace is autotuned at the start by
+ * timing candidate values on the first sigma.
+ *
+ * h_energies[nbatch] (host), d_C[b] (device, n_alpha*n_beta doubles each,
+ * may be NULL to skip the vector; normalised, largest component positive),
+ * h_iters[nbatch] and h_status[nbatch] (host, may be NULL; SQD_OK,
+ * SQD_ENOTCONVERGED or SQD_EBREAKDOWN per subspace).  Returns the first
+ * non-OK subspace status, or an error of the call itself.
+ */
+int sqd_davidson_batched(sqd_ctx *ctx, int nbatch, sqd_tables *const *tables,
+                         const sqd_options *opt, double *h_energies, double *const *d_C,
+                         int *h_iters, int *h_status);
+
+/* The alpha-group scale the last sqd_davidson_batched call chose (host). */
+int sqd_batched_tuning(const sqd_ctx *ctx, double *group_scale);
+
 /* ------------------------------------------------ adjoint: RDMs ----- */
 
 /*

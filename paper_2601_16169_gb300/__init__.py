@@ -24,7 +24,8 @@ import torch
 __all__ = [
     "SQDError", "lib", "library_path", "Context", "Tables", "Options",
     "build_strings", "excitation_tables", "sigma", "davidson", "diagonal", "rdm",
-    "orbital_gradient", "SQDEnergy",
+    "orbital_gradient", "SQDEnergy", "davidson_batched", "batched_tuning",
+    "build_strings_noalloc",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -45,7 +46,7 @@ EXPORTED = [
     "sqd_build_strings", "sqd_excitation_tables", "sqd_free_tables", "sqd_tables_info",
     "sqd_tables_export", "sqd_diagonal", "sqd_sigma", "sqd_davidson", "sqd_rdm",
     "sqd_profile_enable", "sqd_profile_read", "sqd_launch_count", "sqd_orbital_gradient",
-    "sqd_build_strings_noalloc",
+    "sqd_build_strings_noalloc", "sqd_davidson_batched", "sqd_batched_tuning",
 ]
 
 PROFILE_CLASSES = ["same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose", "tables",
@@ -107,6 +108,8 @@ def lib():
     L.sqd_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
     L.sqd_orbital_gradient.argtypes = [vp, vp, vp, vp, vp]
     L.sqd_build_strings_noalloc.argtypes = [vp, vp, i64, i32, i32, vp, ctypes.POINTER(i64)]
+    L.sqd_davidson_batched.argtypes = [vp, i32, vp, ctypes.POINTER(Options), vp, vp, vp, vp]
+    L.sqd_batched_tuning.argtypes = [vp, ctypes.POINTER(dbl)]
     _LIB = L
     return L
 
@@ -329,6 +332,38 @@ def davidson(ctx: Context, tables: Tables, nroots: int = 1, tol_residual: float 
                                           ctypes.byref(it), ctypes.c_void_p(r.ctypes.data)),
                     allow=allow)
     return e, C, it.value, r, rc
+
+
+def davidson_batched(ctx: Context, tables, tol_residual: float = 1e-8,
+                     tol_energy: float = 1e-8, max_iter: int = 200, max_subspace: int = 0,
+                     precond_floor: float = 1e-8, want_vectors: bool = True,
+                     raise_on_nonconvergence: bool = True):
+    """sqd_davidson_batched: ground states of many subspaces in one solve.
+    Returns (energies, list of C tensors or None, iterations, statuses, rc)."""
+    import numpy as np
+    nb = len(tables)
+    handles = (ctypes.c_void_p * nb)(*[t.handle.value for t in tables])
+    Cs = [torch.empty((t.na, t.nb), dtype=torch.float64, device="cuda:%d" % ctx.device)
+          for t in tables] if want_vectors else None
+    ptrs = (ctypes.c_void_p * nb)(*([c.data_ptr() for c in Cs] if Cs else [0] * nb))
+    o = Options(nroots=1, max_iter=max_iter, max_subspace=max_subspace, tol_energy=tol_energy,
+                tol_residual=tol_residual, precond_floor=precond_floor, use_guess=0, reserved=0)
+    e = np.zeros(nb)
+    it = np.zeros(nb, dtype=np.int32)
+    st = np.zeros(nb, dtype=np.int32)
+    allow = () if raise_on_nonconvergence else (SQD_ENOTCONVERGED, SQD_EBREAKDOWN)
+    rc = ctx._check(ctx._lib.sqd_davidson_batched(
+        ctx.handle, nb, handles, ctypes.byref(o), ctypes.c_void_p(e.ctypes.data),
+        ptrs if Cs else None, ctypes.c_void_p(it.ctypes.data), ctypes.c_void_p(st.ctypes.data)),
+        allow=allow)
+    return e, Cs, it, st, rc
+
+
+def batched_tuning(ctx: Context) -> float:
+    """sqd_batched_tuning: alpha-group scale chosen by the last batched solve."""
+    v = ctypes.c_double()
+    ctx._check(ctx._lib.sqd_batched_tuning(ctx.handle, ctypes.byref(v)))
+    return v.value
 
 
 def rdm(ctx: Context, tables: Tables, C: torch.Tensor, two_body: bool = True):

@@ -748,6 +748,28 @@ int sqd_davidson(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, double *h_en
     return davidson_impl(ctx, t, o, h_energies, d_C, h_iters, h_res);
 }
 
+int sqd_davidson_batched(sqd_ctx *ctx, int nbatch, sqd_tables *const *tables,
+                         const sqd_options *o, double *h_energies, double *const *d_C,
+                         int *h_iters, int *h_status) {
+    if (!ctx || !o) return fail_noctx(SQD_EINVAL, "sqd_davidson_batched: NULL argument");
+    if (nbatch < 1 || !tables || !h_energies)
+        return sqd_fail(ctx, SQD_EINVAL, "nbatch >= 1, tables and h_energies are required");
+    if (o->nroots != 1) return sqd_fail(ctx, SQD_EINVAL, "the batched solver finds one root");
+    if (o->max_iter < 0 || !(o->tol_energy >= 0) || !(o->tol_residual >= 0) ||
+        !(o->precond_floor > 0) || o->max_subspace < 0)
+        return sqd_fail(ctx, SQD_EINVAL, "invalid Davidson options");
+    for (int b = 0; b < nbatch; b++)
+        if (!tables[b]) return sqd_fail(ctx, SQD_EINVAL, "tables[%d] is NULL", b);
+    SQD_TRY(use_device(ctx));
+    return davidson_batched_impl(ctx, nbatch, tables, o, h_energies, d_C, h_iters, h_status);
+}
+
+int sqd_batched_tuning(const sqd_ctx *ctx, double *group_scale) {
+    if (!ctx || !group_scale) return fail_noctx(SQD_EINVAL, "sqd_batched_tuning: NULL argument");
+    *group_scale = ctx->batched_group_scale;
+    return SQD_OK;
+}
+
 // ----------------------------------------------------------------- RDMs --
 
 int sqd_rdm(sqd_ctx *ctx, sqd_tables *t, const double *d_C, double *d_rdm1, double *d_rdm2) {

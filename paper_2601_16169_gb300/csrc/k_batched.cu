@@ -1,0 +1,817 @@
+// Batched SQD: many independent subspaces (each its own alpha/beta string
+// sets over one Hamiltonian) solved together for their ground states.
+//
+// The paper solves one subspace per run; SQD itself produces many
+// subsampled subspaces per round (Section I), which is what this serves.
+//
+// Design
+//  - Every Davidson step runs as one launch over all subspaces: the sigma
+//    stages are persistent kernels whose blocks pull (subspace, tile) work
+//    items from an atomic counter; the vector kernels take (subspace,
+//    slice) items; the small dense steps (Jacobi, GD+k restart basis) run
+//    one block per subspace.
+//  - Control lives on the device: each subspace has a state record
+//    (basis size, active flag, theta, residual, ...) that every kernel
+//    reads, so the kernel sequence of an iteration is the same for every
+//    iteration and every subspace.  It is captured once in a CUDA graph and
+//    replayed; the host reads one counter (active subspaces) per replay.
+//  - The only tunable tile parameter (the number of alpha-row groups of the
+//    paired-singles kernel per subspace) is chosen at setup by timing the
+//    candidates on the subspaces' first sigma (autotuning).
+//  - One root per subspace (the ground state), GD+k restart to 3 vectors.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "davidson_body.cuh"
+#include "sigma_body.cuh"
+
+#define BV_SLICE 8192  // vector elements per slice item
+#define BV_THREADS 256
+
+struct bdesc {
+    int64_t na, nb, N, nsl;
+    ss_args ssa;  // alpha side (C, S filled from the state)
+    ss_args ssb;  // beta side on T -> U
+    ab_args ab;   // paired singles (C, S filled from the state)
+    int64_t nch, ngr;
+    double *V, *W, *X, *R, *T, *U;  // V, W: M vectors each
+    double *G, *evals, *evecs, *Yprev, *Z, *partial, *coef;
+    const double *diag;
+};
+
+struct bstate {
+    int m, mprev, active, status, it, restart, newvec, r;
+    double theta, theta_old, rn, nrm2, scale;
+    int64_t guess;
+};
+
+struct bparams {
+    int nprob, M;
+    double tol_r, tol_e, floor_;
+    int max_iter;
+};
+
+__device__ __forceinline__ int find_prob(const int64_t *__restrict__ pre, int nprob,
+                                         int64_t item) {
+    int lo = 0, hi = nprob;  // pre[lo] <= item < pre[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (pre[mid] <= item) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// pull the next work item of a persistent kernel (block-uniform)
+__device__ __forceinline__ int64_t next_item(unsigned long long *counter) {
+    __shared__ int64_t s_item;
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_item = (int64_t)atomicAdd(counter, 1ull);
+    __syncthreads();
+    int64_t it = s_item;
+    __syncthreads();
+    return it;
+}
+
+// ------------------------------------------------------------ sigma stages --
+
+template <bool ALPHA>
+__global__ void __launch_bounds__(256) kb_same_spin(const bdesc *__restrict__ D,
+                                                    const bstate *__restrict__ S,
+                                                    const int64_t *__restrict__ pre, int nprob,
+                                                    unsigned long long *counter) {
+    const int64_t total = pre[nprob];
+    for (;;) {
+        const int64_t item = next_item(counter);
+        if (item >= total) break;
+        const int b = find_prob(pre, nprob, item);
+        if (!S[b].newvec) continue;
+        const bdesc &d = D[b];
+        ss_args a = ALPHA ? d.ssa : d.ssb;
+        if (ALPHA) {
+            const int64_t slot = (int64_t)(S[b].m - 1) * d.N;
+            a.C = d.V + slot;
+            a.S = d.W + slot;
+        } else {
+            a.C = d.T;
+            a.S = d.U;
+        }
+        const int64_t local = item - pre[b];
+        same_spin_tile<ALPHA>(a, local % a.nrows, local / a.nrows);
+    }
+}
+
+// dir 0: new vector (na x nb) -> T (nb x na); dir 1: W slot += U^T
+template <int DIR>
+__global__ void __launch_bounds__(256) kb_transpose(const bdesc *__restrict__ D,
+                                                    const bstate *__restrict__ S,
+                                                    const int64_t *__restrict__ pre, int nprob,
+                                                    unsigned long long *counter) {
+    const int64_t total = pre[nprob];
+    for (;;) {
+        const int64_t item = next_item(counter);
+        if (item >= total) break;
+        const int b = find_prob(pre, nprob, item);
+        if (!S[b].newvec) continue;
+        const bdesc &d = D[b];
+        const int64_t slot = (int64_t)(S[b].m - 1) * d.N;
+        const int64_t rows = DIR == 0 ? d.na : d.nb, cols = DIR == 0 ? d.nb : d.na;
+        const int64_t tx = (cols + 31) / 32;
+        const int64_t local = item - pre[b];
+        const int64_t c0 = (local % tx) * 32, r0 = (local / tx) * 32;
+        if (DIR == 0) transpose_tile<false>(d.V + slot, d.T, rows, cols, c0, r0);
+        else transpose_tile<true>(d.U, d.W + slot, rows, cols, c0, r0);
+    }
+}
+
+__global__ void __launch_bounds__(AB_THREADS, 2) kb_alpha_beta(const bdesc *__restrict__ D,
+                                                               const bstate *__restrict__ S,
+                                                               const int64_t *__restrict__ pre,
+                                                               int nprob,
+                                                               unsigned long long *counter) {
+    const int64_t total = pre[nprob];
+    for (;;) {
+        const int64_t item = next_item(counter);
+        if (item >= total) break;
+        const int b = find_prob(pre, nprob, item);
+        if (!S[b].newvec) continue;
+        const bdesc &d = D[b];
+        ab_args a = d.ab;
+        const int64_t slot = (int64_t)(S[b].m - 1) * d.N;
+        a.C = d.V + slot;
+        a.S = d.W + slot;
+        const int64_t local = item - pre[b];
+        alpha_beta_block(a, local % d.nch, local / d.nch);
+    }
+}
+
+// ---------------------------------------------------------- vector stages --
+
+// decode a slice item: problem, element range
+struct slice_t {
+    int b;
+    int64_t lo, hi, s;
+};
+__device__ __forceinline__ slice_t slice_of(const bdesc *D, const int64_t *pre, int nprob,
+                                            int64_t item) {
+    slice_t r;
+    r.b = find_prob(pre, nprob, item);
+    r.s = item - pre[r.b];
+    r.lo = r.s * BV_SLICE;
+    r.hi = min(D[r.b].N, r.lo + BV_SLICE);
+    return r;
+}
+
+// Ritz vector x = V y0, residual R = W y0 - theta x, partial |R|^2 per slice
+__global__ void __launch_bounds__(BV_THREADS) kb_ritz(const bdesc *__restrict__ D,
+                                                      const bstate *__restrict__ S,
+                                                      const int64_t *__restrict__ pre, int nprob) {
+    __shared__ double red[32];
+    const slice_t sl = slice_of(D, pre, nprob, blockIdx.x);
+    const bstate &st = S[sl.b];
+    if (!st.active) return;
+    const bdesc &d = D[sl.b];
+    const int m = st.m;
+    const double th = d.evals[0];
+    double ss = 0.0;
+    for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) {
+        double x = 0.0, w = 0.0;
+        for (int i = 0; i < m; i++) {
+            const double y = d.evecs[i];
+            x = fma(d.V[(int64_t)i * d.N + n], y, x);
+            w = fma(d.W[(int64_t)i * d.N + n], y, w);
+        }
+        const double r = fma(-th, x, w);
+        d.X[n] = x;
+        d.R[n] = r;
+        ss = fma(r, r, ss);
+    }
+    const double t = block_sum(ss, red);
+    if (threadIdx.x == 0) d.partial[sl.s] = t;
+}
+
+// convergence test and restart decision (one thread per subspace)
+__global__ void kb_state_check(const bdesc *__restrict__ D, bstate *__restrict__ S, bparams P) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= P.nprob) return;
+    bstate &st = S[b];
+    st.newvec = 0;
+    st.restart = 0;
+    if (!st.active) return;
+    const bdesc &d = D[b];
+    double s = 0.0;
+    for (int64_t i = 0; i < d.nsl; i++) s += d.partial[i];
+    st.rn = sqrt(s);
+    st.theta = d.evals[0];
+    if (st.rn <= P.tol_r && fabs(st.theta - st.theta_old) <= P.tol_e) {
+        st.active = 0;
+        st.status = 1;
+        return;
+    }
+    if (st.it >= P.max_iter) {
+        st.active = 0;
+        st.status = SQD_ENOTCONVERGED;
+        return;
+    }
+    st.it++;
+    st.theta_old = st.theta;
+    st.restart = (st.m + 1 > P.M) ? 1 : 0;
+}
+
+// GD+k restart basis Z and the projected G' = Z^T G Z (one block, 128
+// threads, per restarting subspace); otherwise keep the Ritz coefficients
+__global__ void __launch_bounds__(128) kb_restart_basis(const bdesc *__restrict__ D,
+                                                        bstate *__restrict__ S, bparams P) {
+    const int b = blockIdx.x;
+    bstate &st = S[b];
+    if (!st.active) return;
+    const bdesc &d = D[b];
+    const int m = st.m, M = P.M;
+    if (!st.restart) {
+        for (int i = threadIdx.x; i < m; i += blockDim.x) d.Yprev[i] = d.evecs[i];
+        if (threadIdx.x == 0) st.mprev = m;
+        return;
+    }
+    const int r = gdk_block(d.evecs, m, min(2, m), st.mprev ? d.Yprev : nullptr, st.mprev, 1, M,
+                            d.Z, M);
+    // G' = Z^T G Z with G symmetric (upper triangle stored)
+    __shared__ double GZ[JAC_MAX * 3];
+    for (int t = threadIdx.x; t < m * r; t += blockDim.x) {
+        const int i = t % m, j = t / m;
+        double s = 0.0;
+        for (int k = 0; k < m; k++) {
+            const double g = (i <= k) ? d.G[i + (int64_t)k * M] : d.G[k + (int64_t)i * M];
+            s = fma(g, d.Z[k + (int64_t)j * M], s);
+        }
+        GZ[i + j * m] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+        const int i = t % r, j = t / r;
+        if (i > j) continue;
+        double s = 0.0;
+        for (int k = 0; k < m; k++) s = fma(d.Z[k + (int64_t)i * M], GZ[k + j * m], s);
+        d.G[i + (int64_t)j * M] = s;
+    }
+    if (threadIdx.x == 0) {
+        st.r = r;
+        d.Yprev[0] = 1.0;
+        for (int i = 1; i < r; i++) d.Yprev[i] = 0.0;
+        st.mprev = r;
+    }
+}
+
+// in place: V[0..r) = V Z, W[0..r) = W Z for restarting subspaces
+__global__ void __launch_bounds__(BV_THREADS) kb_restart_combine(const bdesc *__restrict__ D,
+                                                                 const bstate *__restrict__ S,
+                                                                 const int64_t *__restrict__ pre,
+                                                                 int nprob, int M) {
+    const slice_t sl = slice_of(D, pre, nprob, blockIdx.x);
+    const bstate &st = S[sl.b];
+    if (!st.active || !st.restart) return;
+    const bdesc &d = D[sl.b];
+    const int m = st.m, r = st.r;
+    for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) {
+        double av[3] = {0.0, 0.0, 0.0}, aw[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < m; i++) {
+            const double v = d.V[(int64_t)i * d.N + n], w = d.W[(int64_t)i * d.N + n];
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                if (j < r) {
+                    const double z = d.Z[i + (int64_t)j * M];
+                    av[j] = fma(v, z, av[j]);
+                    aw[j] = fma(w, z, aw[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            if (j < r) {
+                d.V[(int64_t)j * d.N + n] = av[j];
+                d.W[(int64_t)j * d.N + n] = aw[j];
+            }
+        }
+    }
+}
+
+__global__ void kb_restart_finish(bstate *__restrict__ S, int nprob) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nprob) return;
+    bstate &st = S[b];
+    if (st.active && st.restart) st.m = st.r;
+}
+
+// correction t = R / (theta - H_II) into V[m]
+__global__ void __launch_bounds__(BV_THREADS) kb_precondition(const bdesc *__restrict__ D,
+                                                              const bstate *__restrict__ S,
+                                                              const int64_t *__restrict__ pre,
+                                                              int nprob, double floor_) {
+    const slice_t sl = slice_of(D, pre, nprob, blockIdx.x);
+    const bstate &st = S[sl.b];
+    if (!st.active) return;
+    const bdesc &d = D[sl.b];
+    double *t = d.V + (int64_t)st.m * d.N;
+    for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) {
+        double den = st.theta - d.diag[n];
+        if (fabs(den) < floor_) den = (den < 0.0) ? -floor_ : floor_;
+        t[n] = d.R[n] / den;
+    }
+}
+
+// partial dot products on a slice.  mode 0: V[i] . V[m], i < m (Gram-Schmidt
+// coefficients); mode 1: V[m] . V[m] (norm); mode 2: V[i] . W[m-1], i < m
+// (new column of G, after m was incremented)
+__global__ void __launch_bounds__(BV_THREADS) kb_gram(const bdesc *__restrict__ D,
+                                                      const bstate *__restrict__ S,
+                                                      const int64_t *__restrict__ pre, int nprob,
+                                                      int mode) {
+    __shared__ double red[32];
+    const slice_t sl = slice_of(D, pre, nprob, blockIdx.x);
+    const bstate &st = S[sl.b];
+    if (mode == 2 ? !st.newvec : !st.active) return;
+    const bdesc &d = D[sl.b];
+    const int m = st.m;
+    const double *x = (mode == 2) ? d.W + (int64_t)(m - 1) * d.N : d.V + (int64_t)m * d.N;
+    const int cnt = (mode == 1) ? 1 : m;
+    for (int i = 0; i < cnt; i++) {
+        const double *a = d.V + (int64_t)(mode == 1 ? m : i) * d.N;
+        double s = 0.0;
+        for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) s = fma(a[n], x[n], s);
+        const double t = block_sum(s, red);
+        if (threadIdx.x == 0) d.partial[(int64_t)i * d.nsl + sl.s] = t;
+    }
+}
+
+// sum the partials: one block per subspace, one thread per coefficient
+__global__ void kb_gram_final(const bdesc *__restrict__ D, bstate *__restrict__ S, int mode,
+                              int M) {
+    const int b = blockIdx.x;
+    bstate &st = S[b];
+    if (mode == 2 ? !st.newvec : !st.active) return;
+    const bdesc &d = D[b];
+    const int cnt = (mode == 1) ? 1 : st.m;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        double s = 0.0;
+        for (int64_t k = 0; k < d.nsl; k++) s += d.partial[(int64_t)i * d.nsl + k];
+        if (mode == 0) d.coef[i] = s;
+        else if (mode == 1) st.nrm2 = s;
+        else d.G[i + (int64_t)(st.m - 1) * M] = s;
+    }
+}
+
+// V[m] -= sum_i coef_i V[i]
+__global__ void __launch_bounds__(BV_THREADS) kb_project_out(const bdesc *__restrict__ D,
+                                                             const bstate *__restrict__ S,
+                                                             const int64_t *__restrict__ pre,
+                                                             int nprob) {
+    const slice_t sl = slice_of(D, pre, nprob, blockIdx.x);
+    const bstate &st = S[sl.b];
+    if (!st.active) return;
+    const bdesc &d = D[sl.b];
+    const int m = st.m;
+    double *t = d.V + (int64_t)m * d.N;
+    for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) {
+        double s = 0.0;
+        for (int i = 0; i < m; i++) s = fma(d.V[(int64_t)i * d.N + n], d.coef[i], s);
+        t[n] -= s;
+    }
+}
+
+// keep or drop the orthogonalised correction
+__global__ void kb_state_accept(bstate *__restrict__ S, bparams P) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= P.nprob) return;
+    bstate &st = S[b];
+    st.newvec = 0;
+    if (!st.active) return;
+    const double nrm = sqrt(st.nrm2);
+    if (nrm >= 1e-12) {
+        st.scale = 1.0 / nrm;
+        st.m++;
+        st.newvec = 1;
+    } else {
+        st.active = 0;
+        st.status = (st.rn <= P.tol_r) ? 1 : SQD_EBREAKDOWN;
+    }
+}
+
+__global__ void __launch_bounds__(BV_THREADS) kb_scale_new(const bdesc *__restrict__ D,
+                                                           const bstate *__restrict__ S,
+                                                           const int64_t *__restrict__ pre,
+                                                           int nprob) {
+    const slice_t sl = slice_of(D, pre, nprob, blockIdx.x);
+    const bstate &st = S[sl.b];
+    if (!st.newvec) return;
+    const bdesc &d = D[sl.b];
+    double *v = d.V + (int64_t)(st.m - 1) * d.N;
+    for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) v[n] *= st.scale;
+}
+
+__global__ void __launch_bounds__(256) kb_jacobi(const bdesc *__restrict__ D,
+                                                 const bstate *__restrict__ S, int M) {
+    const int b = blockIdx.x;
+    if (!S[b].active) return;
+    const bdesc &d = D[b];
+    jacobi_block(d.G, M, S[b].m, d.evals, d.evecs);
+}
+
+__global__ void kb_count_active(const bstate *__restrict__ S, int nprob, int *out) {
+    __shared__ int c;
+    if (threadIdx.x == 0) c = 0;
+    __syncthreads();
+    for (int b = threadIdx.x; b < nprob; b += blockDim.x)
+        if (S[b].active) atomicAdd(&c, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) *out = c;
+}
+
+// ---------------------------------------------------------------- setup --
+
+// initial guess: the determinant of lowest H_II (lowest index on ties)
+__global__ void __launch_bounds__(256) kb_guess(const bdesc *__restrict__ D,
+                                                bstate *__restrict__ S) {
+    __shared__ double sv[256];
+    __shared__ int64_t si[256];
+    const int b = blockIdx.x;
+    const bdesc &d = D[b];
+    double bv = INFINITY;
+    int64_t bi = -1;
+    for (int64_t n = threadIdx.x; n < d.N; n += blockDim.x) {
+        const double v = d.diag[n];
+        if (bi < 0 || v < bv) {
+            bv = v;
+            bi = n;
+        }
+    }
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const double v2 = sv[threadIdx.x + o];
+            const int64_t i2 = si[threadIdx.x + o];
+            if (i2 >= 0 && (si[threadIdx.x] < 0 || v2 < sv[threadIdx.x] ||
+                            (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x]))) {
+                sv[threadIdx.x] = v2;
+                si[threadIdx.x] = i2;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        bstate &st = S[b];
+        st = bstate();
+        st.guess = si[0];
+        st.m = 1;
+        st.active = 1;
+        st.newvec = 1;
+        st.theta_old = INFINITY;
+        d.V[si[0]] = 1.0;
+    }
+}
+
+struct batched_plan {
+    int nprob = 0, M = 0;
+    std::vector<bdesc> hdesc;
+    bdesc *D = nullptr;
+    bstate *S = nullptr;
+    int64_t *pre_ssa = nullptr, *pre_ssb = nullptr, *pre_ab = nullptr, *pre_t0 = nullptr,
+            *pre_t1 = nullptr, *pre_vec = nullptr;
+    int64_t tot_vec = 0;
+    unsigned long long *counters = nullptr;  // 5 persistent-kernel queues
+    int *d_active = nullptr;
+    std::vector<void *> owned;  // device allocations
+    std::vector<int64_t *> groups;  // per-problem alpha group arrays (owned)
+};
+
+static int plan_alloc(sqd_ctx *ctx, batched_plan &p, void **ptr, size_t bytes) {
+    cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 8);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return sqd_fail(ctx, e == cudaErrorMemoryAllocation ? SQD_ENOMEM : SQD_ECUDA,
+                        "batched allocation of %zu bytes failed: %s", bytes,
+                        cudaGetErrorString(e));
+    }
+    p.owned.push_back(*ptr);
+    return SQD_OK;
+}
+
+static void plan_free(batched_plan &p) {
+    for (void *q : p.owned) cudaFree(q);
+    p.owned.clear();
+}
+
+static int upload_prefix(sqd_ctx *ctx, batched_plan &p, const std::vector<int64_t> &v,
+                         int64_t **out) {
+    SQD_TRY(plan_alloc(ctx, p, (void **)out, sizeof(int64_t) * v.size()));
+    SQD_CUDA(ctx, cudaMemcpy(*out, v.data(), sizeof(int64_t) * v.size(), cudaMemcpyHostToDevice));
+    return SQD_OK;
+}
+
+// alpha row groups of one subspace: `ng` groups of roughly equal single counts
+static std::vector<int64_t> alpha_groups(const spin_tables *A, int64_t ng) {
+    const std::vector<int64_t> &ao = A->h_off1;
+    const int64_t total = ao[A->n];
+    if (ng > A->n) ng = A->n;
+    if (ng < 1) ng = 1;
+    std::vector<int64_t> g{0};
+    int64_t r = 0;
+    for (int64_t k = 1; k < ng; k++) {
+        const int64_t want = total * k / ng;
+        while (r < A->n && ao[r] < want) r++;
+        if (r > g.back()) g.push_back(r);
+    }
+    g.push_back(A->n);
+    return g;
+}
+
+// launch the three sigma stages for every subspace flagged newvec
+static int launch_sigma_stages(sqd_ctx *ctx, batched_plan &p) {
+    const int n = p.nprob;
+    const int sm = ctx->sm_count;
+    SQD_CUDA(ctx, cudaMemsetAsync(p.counters, 0, sizeof(unsigned long long) * 5, ctx->stream));
+    kb_same_spin<true><<<8 * sm, 256, 0, ctx->stream>>>(p.D, p.S, p.pre_ssa, n, p.counters + 0);
+    SQD_LAUNCHED(ctx);
+    kb_transpose<0><<<8 * sm, dim3(32, 8), 0, ctx->stream>>>(p.D, p.S, p.pre_t0, n,
+                                                             p.counters + 1);
+    SQD_LAUNCHED(ctx);
+    const size_t shm = sizeof(double) * 2 * AB_NA * AB_YW;
+    kb_alpha_beta<<<2 * sm, AB_THREADS, shm, ctx->stream>>>(p.D, p.S, p.pre_ab, n,
+                                                             p.counters + 2);
+    SQD_LAUNCHED(ctx);
+    kb_same_spin<false><<<8 * sm, 256, 0, ctx->stream>>>(p.D, p.S, p.pre_ssb, n,
+                                                         p.counters + 3);
+    SQD_LAUNCHED(ctx);
+    kb_transpose<1><<<8 * sm, dim3(32, 8), 0, ctx->stream>>>(p.D, p.S, p.pre_t1, n,
+                                                             p.counters + 4);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+static int launch_gram(sqd_ctx *ctx, batched_plan &p, int mode) {
+    kb_gram<<<(unsigned)p.tot_vec, BV_THREADS, 0, ctx->stream>>>(p.D, p.S, p.pre_vec, p.nprob,
+                                                                 mode);
+    SQD_LAUNCHED(ctx);
+    kb_gram_final<<<p.nprob, 128, 0, ctx->stream>>>(p.D, p.S, mode, p.M);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// one Davidson iteration for every active subspace (the captured sequence)
+static int launch_iteration(sqd_ctx *ctx, batched_plan &p, const bparams &P) {
+    const int n = p.nprob;
+    const unsigned vb = (unsigned)p.tot_vec;
+    const unsigned tb = (unsigned)((n + 127) / 128);
+    const size_t jshm = sizeof(double) * 2 * (size_t)((p.M + 1) & ~1) * (((p.M + 1) & ~1) + 1);
+    kb_jacobi<<<n, 256, jshm, ctx->stream>>>(p.D, p.S, p.M);
+    SQD_LAUNCHED(ctx);
+    kb_ritz<<<vb, BV_THREADS, 0, ctx->stream>>>(p.D, p.S, p.pre_vec, n);
+    SQD_LAUNCHED(ctx);
+    kb_state_check<<<tb, 128, 0, ctx->stream>>>(p.D, p.S, P);
+    SQD_LAUNCHED(ctx);
+    kb_restart_basis<<<n, 128, 0, ctx->stream>>>(p.D, p.S, P);
+    SQD_LAUNCHED(ctx);
+    kb_restart_combine<<<vb, BV_THREADS, 0, ctx->stream>>>(p.D, p.S, p.pre_vec, n, p.M);
+    SQD_LAUNCHED(ctx);
+    kb_restart_finish<<<tb, 128, 0, ctx->stream>>>(p.S, n);
+    SQD_LAUNCHED(ctx);
+    kb_precondition<<<vb, BV_THREADS, 0, ctx->stream>>>(p.D, p.S, p.pre_vec, n, P.floor_);
+    SQD_LAUNCHED(ctx);
+    for (int pass = 0; pass < 2; pass++) {
+        SQD_TRY(launch_gram(ctx, p, 0));
+        kb_project_out<<<vb, BV_THREADS, 0, ctx->stream>>>(p.D, p.S, p.pre_vec, n);
+        SQD_LAUNCHED(ctx);
+    }
+    SQD_TRY(launch_gram(ctx, p, 1));
+    kb_state_accept<<<tb, 128, 0, ctx->stream>>>(p.S, P);
+    SQD_LAUNCHED(ctx);
+    kb_scale_new<<<vb, BV_THREADS, 0, ctx->stream>>>(p.D, p.S, p.pre_vec, n);
+    SQD_LAUNCHED(ctx);
+    SQD_TRY(launch_sigma_stages(ctx, p));
+    SQD_TRY(launch_gram(ctx, p, 2));
+    kb_count_active<<<1, 256, 0, ctx->stream>>>(p.S, n, p.d_active);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// paired-singles item prefix for a given group scale; updates descriptors
+static int set_groups(sqd_ctx *ctx, batched_plan &p, const std::vector<sqd_tables *> &tabs,
+                      double scale) {
+    std::vector<int64_t> pre{0};
+    for (int b = 0; b < p.nprob; b++) {
+        const sqd_tables *t = tabs[b];
+        int64_t ng = (int64_t)std::llround(std::max(1.0, t->ab.ngroups * scale));
+        std::vector<int64_t> g = alpha_groups(&t->a, ng);
+        int64_t *dg = nullptr;
+        SQD_TRY(plan_alloc(ctx, p, (void **)&dg, sizeof(int64_t) * g.size()));
+        SQD_CUDA(ctx, cudaMemcpy(dg, g.data(), sizeof(int64_t) * g.size(), cudaMemcpyHostToDevice));
+        bdesc &d = p.hdesc[b];
+        d.ab.group_rows = dg;
+        d.ngr = (int64_t)g.size() - 1;
+        const int64_t items = (t->a.nnz1 > 0 && t->b->nnz1 > 0) ? d.nch * d.ngr : 0;
+        pre.push_back(pre.back() + items);
+    }
+    SQD_CUDA(ctx, cudaMemcpy(p.D, p.hdesc.data(), sizeof(bdesc) * p.nprob, cudaMemcpyHostToDevice));
+    SQD_TRY(upload_prefix(ctx, p, pre, &p.pre_ab));
+    return SQD_OK;
+}
+
+int davidson_batched_impl(sqd_ctx *ctx, int nprob, sqd_tables *const *tables,
+                          const sqd_options *o, double *h_energies, double *const *d_C,
+                          int *h_iters, int *h_status) {
+    batched_plan p;
+    p.nprob = nprob;
+    p.M = o->max_subspace > 0 ? std::min(o->max_subspace, 112) : 16;
+    if (p.M < 4) return sqd_fail(ctx, SQD_EINVAL, "max_subspace must be >= 4");
+    std::vector<sqd_tables *> tabs(tables, tables + nprob);
+    p.hdesc.resize(nprob);
+    std::vector<int64_t> pssa{0}, pssb{0}, pt0{0}, pt1{0}, pvec{0};
+    const int M = p.M;
+    int rc = SQD_OK;
+    auto fail = [&](int r) {
+        cudaStreamSynchronize(ctx->stream);
+        plan_free(p);
+        return r;
+    };
+    for (int b = 0; b < nprob; b++) {
+        sqd_tables *t = tabs[b];
+        bdesc &d = p.hdesc[b];
+        d.na = t->a.n;
+        d.nb = t->b->n;
+        d.N = d.na * d.nb;
+        const int Mb = (int)std::min<int64_t>(M, d.N);
+        (void)Mb;
+        d.nsl = (d.N + BV_SLICE - 1) / BV_SLICE;
+        void *q;
+#define BA(field, count)                                                             \
+    if ((rc = plan_alloc(ctx, p, &q, sizeof(double) * (size_t)(count))) != SQD_OK)  \
+        return fail(rc);                                                             \
+    d.field = (double *)q;
+        BA(V, (int64_t)M * d.N);
+        BA(W, (int64_t)M * d.N);
+        BA(X, d.N);
+        BA(R, d.N);
+        BA(T, d.N);
+        BA(U, d.N);
+        BA(G, (int64_t)M * M);
+        BA(evals, M);
+        BA(evecs, (int64_t)M * M);
+        BA(Yprev, M);
+        BA(Z, (int64_t)M * 3);
+        BA(partial, (int64_t)M * d.nsl);
+        BA(coef, M);
+#undef BA
+        if ((rc = (cudaMemsetAsync(d.V, 0, sizeof(double) * d.N, ctx->stream) == cudaSuccess
+                       ? SQD_OK
+                       : SQD_ECUDA)) != SQD_OK)
+            return fail(sqd_fail(ctx, rc, "memset failed"));
+        if (!t->diag) return fail(sqd_fail(ctx, SQD_EINVAL, "table without diagonal"));
+        d.diag = t->diag;
+        d.ssa = make_ss_args(&t->a, t->b, d.na, d.nb, nullptr, nullptr, t->diag);
+        d.ssb = make_ss_args(t->b, &t->a, d.nb, d.na, nullptr, nullptr, nullptr);
+        d.ab = make_ab_args(t, nullptr, nullptr);
+        d.nch = t->ab.nchunks;
+        d.ngr = t->ab.ngroups;
+        pssa.push_back(pssa.back() + d.na * ((d.nb + 255) / 256));
+        pssb.push_back(pssb.back() + d.nb * ((d.na + 255) / 256));
+        pt0.push_back(pt0.back() + ((d.nb + 31) / 32) * ((d.na + 31) / 32));
+        pt1.push_back(pt1.back() + ((d.na + 31) / 32) * ((d.nb + 31) / 32));
+        pvec.push_back(pvec.back() + d.nsl);
+    }
+    p.tot_vec = pvec.back();
+    if (p.tot_vec > 2147483647LL) return fail(sqd_fail(ctx, SQD_EINVAL, "batch too large"));
+    if ((rc = plan_alloc(ctx, p, (void **)&p.D, sizeof(bdesc) * nprob)) != SQD_OK) return fail(rc);
+    if ((rc = plan_alloc(ctx, p, (void **)&p.S, sizeof(bstate) * nprob)) != SQD_OK) return fail(rc);
+    if ((rc = plan_alloc(ctx, p, (void **)&p.counters, sizeof(unsigned long long) * 8)) != SQD_OK)
+        return fail(rc);
+    if ((rc = plan_alloc(ctx, p, (void **)&p.d_active, sizeof(int))) != SQD_OK) return fail(rc);
+    if ((rc = upload_prefix(ctx, p, pssa, &p.pre_ssa)) != SQD_OK) return fail(rc);
+    if ((rc = upload_prefix(ctx, p, pssb, &p.pre_ssb)) != SQD_OK) return fail(rc);
+    if ((rc = upload_prefix(ctx, p, pt0, &p.pre_t0)) != SQD_OK) return fail(rc);
+    if ((rc = upload_prefix(ctx, p, pt1, &p.pre_t1)) != SQD_OK) return fail(rc);
+    if ((rc = upload_prefix(ctx, p, pvec, &p.pre_vec)) != SQD_OK) return fail(rc);
+
+    // kernel attributes (dynamic shared memory)
+    const size_t abshm = sizeof(double) * 2 * AB_NA * AB_YW;
+    const int MM = (M + 1) & ~1;
+    const size_t jshm = sizeof(double) * 2 * (size_t)MM * (MM + 1);
+    if (cudaFuncSetAttribute(kb_alpha_beta, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)abshm) != cudaSuccess ||
+        cudaFuncSetAttribute(kb_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)jshm) != cudaSuccess)
+        return fail(sqd_fail(ctx, SQD_ECUDA, "cannot set shared memory limits"));
+
+    // --- autotune the paired-singles group scale on the first sigma -----
+    const double cand[] = {0.125, 0.25, 0.5, 1.0};
+    double best_ms = INFINITY, best = 1.0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (double sc : cand) {
+        if ((rc = set_groups(ctx, p, tabs, sc)) != SQD_OK) return fail(rc);
+        kb_guess<<<nprob, 256, 0, ctx->stream>>>(p.D, p.S);
+        SQD_LAUNCHED(ctx);
+        cudaEventRecord(e0, ctx->stream);
+        if ((rc = launch_sigma_stages(ctx, p)) != SQD_OK) return fail(rc);
+        cudaEventRecord(e1, ctx->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess)
+            return fail(sqd_fail(ctx, SQD_ECUDA, "sigma stage failed: %s",
+                                 cudaGetErrorString(cudaGetLastError())));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = sc;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->batched_group_scale = best;
+    if ((rc = set_groups(ctx, p, tabs, best)) != SQD_OK) return fail(rc);
+
+    // --- initial guess, its sigma and G[0][0] ------------------------------
+    prof_begin(ctx, PROF_DAVIDSON);
+    kb_guess<<<nprob, 256, 0, ctx->stream>>>(p.D, p.S);
+    SQD_LAUNCHED(ctx);
+    if ((rc = launch_sigma_stages(ctx, p)) != SQD_OK) return fail(rc);
+    if ((rc = launch_gram(ctx, p, 2)) != SQD_OK) return fail(rc);
+
+    bparams P;
+    P.nprob = nprob;
+    P.M = M;
+    P.tol_r = o->tol_residual;
+    P.tol_e = o->tol_energy;
+    P.floor_ = o->precond_floor;
+    P.max_iter = o->max_iter;
+
+    // --- capture one iteration, replay until no subspace is active ---------
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(sqd_fail(ctx, SQD_ECUDA, "cannot create capture stream"));
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+        return fail(sqd_fail(ctx, SQD_ECUDA, "setup failed: %s",
+                             cudaGetErrorString(cudaGetLastError())));
+    cudaStream_t user = ctx->stream;
+    ctx->stream = cap;
+    int64_t before = ctx->launches;
+    bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    int irc = ok ? launch_iteration(ctx, p, P) : SQD_ECUDA;
+    ok = (cudaStreamEndCapture(cap, &graph) == cudaSuccess) && ok && irc == SQD_OK;
+    const int64_t per_iter = ctx->launches - before;
+    ctx->launches = before;
+    ctx->stream = user;
+    if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (!ok) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cap);
+        cudaGetLastError();
+        return fail(sqd_fail(ctx, SQD_ECUDA, "graph capture of the batched iteration failed"));
+    }
+    int active = nprob, iters = 0;
+    while (active > 0 && iters <= o->max_iter + 1) {
+        if (cudaGraphLaunch(exec, ctx->stream) != cudaSuccess) break;
+        ctx->launches += per_iter;
+        cudaMemcpyAsync(&active, p.d_active, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) break;
+        iters++;
+    }
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap);
+    prof_end(ctx, 0.0, 0.0);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess)
+        return fail(sqd_fail(ctx, SQD_ECUDA, "batched Davidson failed: %s",
+                             cudaGetErrorString(ce)));
+
+    // --- outputs -----------------------------------------------------------
+    std::vector<bstate> hs(nprob);
+    if (cudaMemcpy(hs.data(), p.S, sizeof(bstate) * nprob, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(sqd_fail(ctx, SQD_ECUDA, "state copy failed"));
+    double *work = nullptr;
+    if ((rc = plan_alloc(ctx, p, (void **)&work, sizeof(double) * (3 * 4 * ctx->sm_count + 8))) !=
+        SQD_OK)
+        return fail(rc);
+    int status = SQD_OK;
+    for (int b = 0; b < nprob; b++) {
+        const bdesc &d = p.hdesc[b];
+        if (d_C && d_C[b]) {
+            if (cudaMemcpyAsync(d_C[b], d.X, sizeof(double) * d.N, cudaMemcpyDeviceToDevice,
+                                ctx->stream) != cudaSuccess)
+                return fail(sqd_fail(ctx, SQD_ECUDA, "output copy failed"));
+            if ((rc = launch_fix_phase(ctx, d_C[b], d.N, 1, d.N, work)) != SQD_OK) return fail(rc);
+        }
+        h_energies[b] = hs[b].theta;
+        if (h_iters) h_iters[b] = hs[b].it;
+        const int st = hs[b].status == 1 ? SQD_OK
+                                         : (hs[b].status == 0 ? SQD_ENOTCONVERGED : hs[b].status);
+        if (h_status) h_status[b] = st;
+        if (st != SQD_OK && status == SQD_OK) status = st;
+    }
+    cudaStreamSynchronize(ctx->stream);
+    plan_free(p);
+    if (status != SQD_OK)
+        return sqd_fail(ctx, status, "some subspaces did not converge (see h_status)");
+    return SQD_OK;
+}

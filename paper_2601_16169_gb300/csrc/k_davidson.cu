@@ -5,23 +5,8 @@
 // order so results do not depend on scheduling.
 #include <cmath>
 
-#include "sqd_internal.cuh"
+#include "davidson_body.cuh"
 
-#define RED_THREADS 256
-
-__device__ __forceinline__ double block_sum(double v, double *sh) {
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < (int)(blockDim.x >> 5); i++) r += sh[i];
-    }
-    __syncthreads();
-    return r;  // valid in thread 0
-}
 
 int multidot_blocks(int64_t n) {
     int64_t b = (n + 4095) / 4096;
@@ -192,119 +177,10 @@ int launch_scale(sqd_ctx *ctx, double *x, int64_t n, const double *s_dev, int in
 // all row rotations.  Sweeps until the off-diagonal norm is negligible.
 // Output: evals ascending, evecs column-major (evecs[i + j*m] = Y_ij).
 
-#define JAC_MAX 112
-
 __global__ void __launch_bounds__(1024) k_jacobi(const double *__restrict__ G, int ldg, int m,
                                                  double *__restrict__ evals,
                                                  double *__restrict__ evecs) {
-    // A and Q live in dynamic shared memory, (M) x (M+1) doubles each
-    extern __shared__ double jac_sh[];
-    __shared__ double cs[JAC_MAX / 2], sn[JAC_MAX / 2];
-    __shared__ int pp[JAC_MAX / 2], qq[JAC_MAX / 2];
-    __shared__ double red[32];
-    __shared__ int done;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int M = (m + 1) & ~1;  // even size; a padding row/col stays zero
-    const int LD = M + 1;
-    double *Ab = jac_sh, *Qb = jac_sh + (size_t)M * LD;
-#define A(i, j) Ab[(i) * LD + (j)]
-#define Q(i, j) Qb[(i) * LD + (j)]
-    // only the upper triangle G[i + j*ldg], i <= j, is read
-    for (int t = tid; t < M * M; t += nt) {
-        int i = t / M, j = t % M;
-        double v = 0.0;
-        if (i < m && j < m) v = (i <= j) ? G[i + (int64_t)j * ldg] : G[j + (int64_t)i * ldg];
-        A(i, j) = v;
-        Q(i, j) = (i == j) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    const int npair = M / 2;
-    for (int sweep = 0; sweep < 60; sweep++) {
-        // convergence: off-diagonal Frobenius norm vs diagonal
-        double off = 0.0, dia = 0.0;
-        for (int t = tid; t < M * M; t += nt) {
-            int i = t / M, j = t % M;
-            double v = A(i, j);
-            if (i != j) off += v * v; else dia += v * v;
-        }
-        double offs = block_sum(off, red);
-        double dias = block_sum(dia, red);
-        if (tid == 0) done = (offs <= 1e-30 * dias || offs == 0.0) ? 1 : 0;
-        __syncthreads();
-        if (done) break;
-        for (int step = 0; step < M - 1; step++) {
-            if (tid < npair) {
-                // round-robin: player M-1 fixed, the others rotate
-                int a, b;
-                if (tid == 0) {
-                    a = step;
-                    b = M - 1;
-                } else {
-                    a = (step + tid) % (M - 1);
-                    b = (step + M - 1 - tid) % (M - 1);
-                }
-                int p = min(a, b), q = max(a, b);
-                double apq = A(p, q);
-                double c = 1.0, s = 0.0;
-                if (apq != 0.0) {
-                    double tau = (A(q, q) - A(p, p)) / (2.0 * apq);
-                    double t = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau))
-                                            : -1.0 / (-tau + sqrt(1.0 + tau * tau));
-                    c = 1.0 / sqrt(1.0 + t * t);
-                    s = t * c;
-                }
-                pp[tid] = p;
-                qq[tid] = q;
-                cs[tid] = c;
-                sn[tid] = s;
-            }
-            __syncthreads();
-            // columns: A <- A J, Q <- Q J
-            for (int t = tid; t < M * npair; t += nt) {
-                int r = t / npair, k = t % npair;
-                int p = pp[k], q = qq[k];
-                double c = cs[k], s = sn[k];
-                double ap = A(r, p), aq = A(r, q);
-                A(r, p) = c * ap - s * aq;
-                A(r, q) = s * ap + c * aq;
-                double qp = Q(r, p), qv = Q(r, q);
-                Q(r, p) = c * qp - s * qv;
-                Q(r, q) = s * qp + c * qv;
-            }
-            __syncthreads();
-            // rows: A <- J^T A
-            for (int t = tid; t < M * npair; t += nt) {
-                int col = t / npair, k = t % npair;
-                int p = pp[k], q = qq[k];
-                double c = cs[k], s = sn[k];
-                double ap = A(p, col), aq = A(q, col);
-                A(p, col) = c * ap - s * aq;
-                A(q, col) = s * ap + c * aq;
-            }
-            __syncthreads();
-        }
-    }
-    // sort ascending (selection of the order by one thread), write out
-    __shared__ int order[JAC_MAX];
-    if (tid == 0) {
-        for (int i = 0; i < m; i++) order[i] = i;
-        for (int i = 0; i < m; i++) {
-            int best = i;
-            for (int j = i + 1; j < m; j++) {
-                double dj = A(order[j], order[j]), db = A(order[best], order[best]);
-                if (dj < db || (dj == db && order[j] < order[best])) best = j;
-            }
-            int tmp = order[i];
-            order[i] = order[best];
-            order[best] = tmp;
-        }
-    }
-    __syncthreads();
-    for (int t = tid; t < m * m; t += nt) {
-        int i = t % m, j = t / m;  // evecs[i + j*m] = Q(i, order[j])
-        evecs[i + (int64_t)j * m] = Q(i, order[j]);
-    }
-    for (int j = tid; j < m; j += nt) evals[j] = A(order[j], order[j]);
+    jacobi_block(G, ldg, m, evals, evecs);
 }
 
 int launch_jacobi_eigh(sqd_ctx *ctx, const double *G, int ldg, int m, double *evals,
@@ -425,39 +301,8 @@ __global__ void __launch_bounds__(128) k_gdk_basis(const double *__restrict__ Y,
                                                    const double *__restrict__ P, int mp, int k,
                                                    int ldp, double *__restrict__ Z, int ldz,
                                                    int *__restrict__ r_out) {
-    __shared__ double p[JAC_MAX];
-    __shared__ double red[32];
-    __shared__ double coef;
-    const int i = threadIdx.x;
-    for (int j = 0; j < m2; j++)
-        if (i < m) Z[i + (int64_t)j * ldz] = Y[i + (int64_t)j * m];
-    __syncthreads();
-    int r = m2;
-    for (int j = 0; j < k; j++) {
-        if (i < m) p[i] = (i < mp && P) ? P[i + (int64_t)j * ldp] : 0.0;
-        __syncthreads();
-        for (int pass = 0; pass < 2; pass++) {
-            for (int c = 0; c < r; c++) {
-                double v = (i < m) ? Z[i + (int64_t)c * ldz] * p[i] : 0.0;
-                double d = block_sum(v, red);
-                if (i == 0) coef = d;
-                __syncthreads();
-                if (i < m) p[i] -= coef * Z[i + (int64_t)c * ldz];
-                __syncthreads();
-            }
-        }
-        double nv = (i < m) ? p[i] * p[i] : 0.0;
-        double n2 = block_sum(nv, red);
-        if (i == 0) coef = n2;
-        __syncthreads();
-        double nrm = sqrt(coef);
-        if (nrm > 1e-8) {  // uniform across the block
-            if (i < m) Z[i + (int64_t)r * ldz] = p[i] / nrm;
-            r++;
-        }
-        __syncthreads();
-    }
-    if (i == 0) *r_out = r;
+    int r = gdk_block(Y, m, m2, P, mp, k, ldp, Z, ldz);
+    if (threadIdx.x == 0) *r_out = r;
 }
 
 int launch_gdk_basis(sqd_ctx *ctx, const double *Y, int m, int m2, const double *P, int mp,

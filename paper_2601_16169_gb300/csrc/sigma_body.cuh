@@ -1,0 +1,225 @@
+// Device bodies of the sigma kernels, shared by the single-problem kernels
+// (k_sigma.cu) and the persistent batched kernels (k_batched.cu).
+#pragma once
+
+#include "sqd_internal.cuh"
+
+// same-spin product over one table set (rows) and the other spin (columns)
+struct ss_args {
+    int64_t nrows, ncols;
+    const double *C;
+    double *S;
+    const int64_t *off1;
+    const int32_t *tgt1;
+    const uint16_t *pq1;
+    const int8_t *sgn1;
+    const double *val1;
+    const int64_t *off2;
+    const int32_t *tgt2;
+    const double *val2;
+    const double *W;     // [norb^2][ncols] coupling of the column spin
+    const double *diag;  // [nrows][ncols] or null
+};
+
+// paired alpha x beta singles
+struct ab_args {
+    int64_t nb;
+    int norb2;
+    const int64_t *a_off;
+    const int32_t *a_tgt;
+    const uint16_t *a_pq;
+    const int8_t *a_sgn;
+    const int64_t *b_off;
+    const int32_t *b_tgt;
+    const uint16_t *b_pq;
+    const int8_t *b_sgn;
+    const int64_t *chunk_rows;
+    const int64_t *group_rows;
+    const double *C;
+    double *S;
+    const double *V;
+};
+
+ss_args make_ss_args(const spin_tables *R, const spin_tables *Cc, int64_t nrows, int64_t ncols,
+                     const double *C, double *S, const double *diag);
+ab_args make_ab_args(const sqd_tables *t, const double *C, double *S);
+
+#define AB_THREADS 256
+#define AB_EPT 16                          // beta entries per thread
+#define AB_ECAP (AB_THREADS * AB_EPT)      // beta entries per block
+#define AB_YW 256                          // beta rows (slab width) per block
+#define AB_NA 16                           // alpha singles staged per batch
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Work items of a block are (alpha row, batch of AB_NA alpha singles) pairs
+// over the rows of its group that have singles, in order.  The slabs of
+// item i+1 are copied (cp.async) while item i is computed.
+struct ab_item {
+    int64_t ia, ab, a1;  // row, first single of the batch, end of the row's singles
+};
+
+__device__ __forceinline__ bool ab_next(const int64_t *__restrict__ a_off, int64_t g1,
+                                        ab_item &it) {
+    it.ab += AB_NA;
+    if (it.ab < it.a1) return true;
+    for (int64_t ia = it.ia + 1; ia < g1; ia++) {
+        int64_t a0 = a_off[ia], a1 = a_off[ia + 1];
+        if (a1 > a0) {
+            it.ia = ia;
+            it.ab = a0;
+            it.a1 = a1;
+            return true;
+        }
+    }
+    it.ia = g1;
+    return false;
+}
+
+// One (row, 256-column tile) of the same-spin product; blockDim.x == 256.
+template <bool DIAG>
+__device__ __forceinline__ void same_spin_tile(const ss_args &a, int64_t row, int64_t tile) {
+    const int64_t ncols = a.ncols;
+    const int64_t col = tile * 256 + threadIdx.x;
+    if (col >= ncols) return;
+    const double *__restrict__ C = a.C;
+    double acc = 0.0;
+    if (DIAG) acc = a.diag[row * ncols + col] * C[row * ncols + col];
+    const int64_t s1 = a.off1[row], e1 = a.off1[row + 1];
+    for (int64_t e = s1; e < e1; e++) {
+        int64_t J = a.tgt1[e];
+        double c = C[J * ncols + col];
+        double w = a.W[(int64_t)a.pq1[e] * ncols + col];
+        w = (a.sgn1[e] < 0) ? -w : w;
+        acc = fma(a.val1[e], c, acc);
+        acc = fma(w, c, acc);
+    }
+    const int64_t s2 = a.off2[row], e2 = a.off2[row + 1];
+    for (int64_t e = s2; e < e2; e++) acc = fma(a.val2[e], C[(int64_t)a.tgt2[e] * ncols + col], acc);
+    a.S[row * ncols + col] = acc;
+}
+
+// One block's work of the paired-singles product: beta chunk `chunk`,
+// alpha row group `group` (dynamic shared memory: 2*AB_NA*AB_YW doubles).
+__device__ __forceinline__ void alpha_beta_block(const ab_args &a, int64_t chunk, int64_t group) {
+    // double-buffered slabs in dynamic shared memory: [2][AB_NA][AB_YW] doubles
+    extern __shared__ double ab_dyn[];
+    double(*slab)[AB_NA][AB_YW] = reinterpret_cast<double(*)[AB_NA][AB_YW]>(ab_dyn);
+    __shared__ int64_t sh_vrow[2][AB_NA];
+    __shared__ uint32_t sh_sa[2][AB_NA];
+    __shared__ int64_t sh_off[AB_YW + 1];
+
+    const int tid = threadIdx.x;
+    const int64_t y0 = a.chunk_rows[chunk], y1 = a.chunk_rows[chunk + 1];
+    const int width = (int)(y1 - y0);
+    for (int t = tid; t <= width; t += AB_THREADS) sh_off[t] = a.b_off[y0 + t];
+    __syncthreads();
+    const int64_t e0 = sh_off[0], e1 = sh_off[width];
+
+    // this thread's beta entries: neighbour Ib and packed
+    // (V column | slab column << 12 | sign << 31)
+    int32_t ib[AB_EPT];
+    uint32_t info[AB_EPT];
+    double acc[AB_EPT];
+#pragma unroll
+    for (int k = 0; k < AB_EPT; k++) {
+        int64_t e = e0 + tid + (int64_t)k * AB_THREADS;
+        ib[k] = -1;
+        info[k] = 0;
+        if (e < e1) {
+            int lo = 0, hi = width;  // sh_off[lo] <= e < sh_off[hi]
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (sh_off[mid] <= e) lo = mid; else hi = mid;
+            }
+            ib[k] = a.b_tgt[e];
+            info[k] = (uint32_t)a.b_pq[e] | ((uint32_t)lo << 12) | ((a.b_sgn[e] < 0) ? 0x80000000u : 0u);
+        }
+        acc[k] = 0.0;
+    }
+
+    const int64_t g0 = a.group_rows[group], g1 = a.group_rows[group + 1];
+    // stage the slabs and alpha data of one item into buffer `buf`
+    auto stage = [&](const ab_item &it, int buf) {
+        const int nbat = (int)min((int64_t)AB_NA, it.a1 - it.ab);
+        if (tid < nbat) {
+            sh_vrow[buf][tid] = (int64_t)a.a_pq[it.ab + tid] * a.norb2;
+            sh_sa[buf][tid] = (a.a_sgn[it.ab + tid] < 0) ? 1u : 0u;
+        }
+        for (int idx = tid; idx < nbat * width; idx += AB_THREADS) {
+            int aa = idx / width, j = idx - aa * width;
+            cp_async8(&slab[buf][aa][j], a.C + (int64_t)a.a_tgt[it.ab + aa] * a.nb + y0 + j);
+        }
+        cp_async_commit();
+    };
+
+    ab_item cur;
+    cur.ia = g0 - 1;
+    cur.ab = 0;
+    cur.a1 = 0;
+    bool have = ab_next(a.a_off, g1, cur);
+    if (have) stage(cur, 0);
+    int buf = 0;
+    while (have) {
+        ab_item nxt = cur;
+        bool more = ab_next(a.a_off, g1, nxt);
+        if (more) stage(nxt, buf ^ 1);
+        else cp_async_commit();  // keep the group count uniform
+        cp_async_wait<1>();
+        __syncthreads();  // slabs of `cur` visible to all threads
+        const int nbat = (int)min((int64_t)AB_NA, cur.a1 - cur.ab);
+        for (int ai = 0; ai < nbat; ai++) {
+            const double *vr = a.V + sh_vrow[buf][ai];
+            const uint32_t sa = sh_sa[buf][ai] << 31;
+            const double *sl = slab[buf][ai];
+#pragma unroll
+            for (int k = 0; k < AB_EPT; k++) {
+                const uint32_t inf = info[k];
+                double v = __ldg(vr + (inf & 0xfffu));
+                unsigned long long bits = (unsigned long long)__double_as_longlong(v) ^
+                                          ((unsigned long long)((inf ^ sa) & 0x80000000u) << 32);
+                acc[k] = fma(__longlong_as_double((long long)bits), sl[(inf >> 12) & 0x1ffu], acc[k]);
+            }
+        }
+        if (cur.ab + AB_NA >= cur.a1) {  // last batch of this alpha row: flush
+#pragma unroll
+            for (int k = 0; k < AB_EPT; k++) {
+                if (ib[k] >= 0) atomicAdd(&a.S[cur.ia * a.nb + ib[k]], acc[k]);
+                acc[k] = 0.0;
+            }
+        }
+        __syncthreads();  // buffer `buf` is reused by the item after next
+        cur = nxt;
+        have = more;
+        buf ^= 1;
+    }
+    cp_async_wait<0>();
+}
+
+// out[c][r] (+)= in[r][c] for one 32 x 32 tile at (row r0, column c0); in is
+// rows x cols; blockDim = (32, 8).
+template <bool ADD>
+__device__ __forceinline__ void transpose_tile(const double *__restrict__ in,
+                                               double *__restrict__ out, int64_t rows,
+                                               int64_t cols, int64_t c0, int64_t r0) {
+    __shared__ double tile[32][33];
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        int64_t r = r0 + i, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[i][threadIdx.x] = in[r * cols + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) {
+            if (ADD) out[c * rows + r] += tile[threadIdx.x][i];
+            else out[c * rows + r] = tile[threadIdx.x][i];
+        }
+    }
+    __syncthreads();
+}

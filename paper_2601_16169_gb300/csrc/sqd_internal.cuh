@@ -42,6 +42,7 @@ struct sqd_ctx {
     double cls_flops[PROF_NCLASS] = {0};
     double cls_bytes[PROF_NCLASS] = {0};
     double cls_ms[PROF_NCLASS] = {0};
+    double batched_group_scale = 0.0;    // last autotuned alpha-group scale
 };
 
 // Time the launches between prof_begin/prof_end as one region of class cls
@@ -203,6 +204,11 @@ int launch_fix_phase(sqd_ctx *, double *X, int64_t ld, int k, int64_t n, double 
 int launch_gdk_basis(sqd_ctx *, const double *Y, int m, int m2, const double *P, int mp, int k,
                      int ldp, double *Z, int ldz, int *r_dev);
 int launch_identity_cols(sqd_ctx *, double *Y, int r, int k, int ld);
+
+// batched
+int davidson_batched_impl(sqd_ctx *ctx, int nprob, sqd_tables *const *tables,
+                          const sqd_options *o, double *h_energies, double *const *d_C,
+                          int *h_iters, int *h_status);
 
 // rdm
 int launch_rdm(sqd_ctx *, const sqd_tables *t, const double *C, double *rdm1, double *rdm2);

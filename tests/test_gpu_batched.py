@@ -1,0 +1,77 @@
+"""Batched ground states of many independent subspaces (one captured graph
+per iteration, persistent work-queue sigma) against one sqd_davidson solve
+per subspace.  Bars: |dE| <= 1e-9 Ha; |<x_batched, x_single>| >= 1 - 1e-8."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import sqd_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sqd():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2601_16169_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(sqd):
+    torch.cuda.set_device(0)
+    return sqd.Context(0)
+
+
+def _tables(sqd, ctx, w):
+    s = torch.tensor(w.strings_a.view(np.int64), device="cuda")
+    return sqd.excitation_tables(ctx, w.norb, s, w.nelec_a, s, w.nelec_b,
+                                 torch.tensor(w.h, device="cuda"),
+                                 torch.tensor(w.V, device="cuda"), 0.0)
+
+
+def _compare(sqd, ctx, subs, tol_r=1e-8):
+    tabs = [_tables(sqd, ctx, w) for w in subs]
+    e, Cs, it, st, rc = sqd.davidson_batched(ctx, tabs, tol_residual=tol_r, tol_energy=1e-10)
+    assert rc == 0 and np.all(st == 0)
+    assert 0.0 < sqd.batched_tuning(ctx) <= 1.0
+    for b, t in enumerate(tabs):
+        e1, X1, _, _, _ = sqd.davidson(ctx, t, nroots=1, tol_residual=tol_r, tol_energy=1e-10)
+        assert abs(e[b] - e1[0]) <= 1e-9, (b, e[b], e1[0])
+        ov = abs(float((Cs[b].reshape(-1) * X1[0].reshape(-1)).sum()))
+        assert ov >= 1 - 1e-8
+        assert abs(float(Cs[b].norm()) - 1.0) <= 1e-12
+        t.close()
+    return e
+
+
+def test_batched_matches_sequential_small_uneven(sqd, ctx):
+    subs = si.batched_workload(nbatch=7, sizes=[30, 200, 55, 120, 8, 75, 160])
+    e = _compare(sqd, ctx, subs)
+    # the smallest space is checked against LAPACK too
+    w = subs[4]
+    H = oracle.dense_h(w.norb, w.h, w.V, 0.0, w.strings_a, w.strings_b)
+    assert abs(e[4] - np.linalg.eigvalsh(H)[0]) <= 1e-9
+
+
+def test_batched_degenerate_sizes(sqd, ctx):
+    # one-string and two-string sets (1 and 4 determinants): the basis stops
+    # growing at the space dimension and the solver still converges
+    h, V = si.make_integrals(29, 58, 1001)
+    base = si.batched_workload(nbatch=2, sizes=[40, 40])
+    ws = []
+    for strings in (base[0].strings_a[:1], base[0].strings_a[:2], base[1].strings_a):
+        w = si.Workload(name="deg", norb=29, nelec_a=5, nelec_b=5, h=h, V=V, raw_a=strings,
+                        raw_b=strings, strings_a=strings, strings_b=strings)
+        ws.append(w)
+    e = _compare(sqd, ctx, ws)
+    d = oracle.diag(29, h, V, 0.0, ws[0].strings_a, ws[0].strings_b)
+    assert abs(e[0] - d[0]) <= 1e-12
+
+
+def test_batched_config3_sample(sqd, ctx):
+    # a sample of the 64-subspace workload (its first 6 subspaces, 4e4-9e6 dets)
+    subs = si.batched_workload(nbatch=64)[:6]
+    _compare(sqd, ctx, subs, tol_r=1e-7)
