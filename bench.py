@@ -78,6 +78,8 @@ def _args():
                         "batched: the 64-subspace workload in one batched solve vs one "
                         "solve per subspace")
     p.add_argument("--nbatch", type=int, default=64)
+    p.add_argument("--stored", action="store_true",
+                   help="sigma mode: apply the stored H (sparse matrix) instead")
     return p.parse_args()
 
 
@@ -349,8 +351,12 @@ def run_sigma_only(args, rank, world, local_rank):
     C = torch.from_numpy(si.random_vectors(1, w.ndet, 13).reshape(
         w.strings_a.size, w.strings_b.size)).to(dev)
     S = torch.empty_like(C)
+    apply = sqd.sigma
+    if getattr(args, "stored", False):
+        sqd.stored_h_build(ctx, t)
+        apply = sqd.sigma_stored
     for _ in range(args.warmup):
-        sqd.sigma(ctx, t, C, S)
+        apply(ctx, t, C, S)
     torch.cuda.synchronize(dev)
     ctx.profile(True)
     clk = ClockSampler(local_rank)
@@ -359,7 +365,7 @@ def run_sigma_only(args, rank, world, local_rank):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        sqd.sigma(ctx, t, C, S)
+        apply(ctx, t, C, S)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     clocks = clk.stop()
@@ -380,6 +386,13 @@ def run_sigma_only(args, rank, world, local_rank):
                        for k, v in sig.items()},
            "transpose_ms": prof["transpose"]["ms"] / max(1, args.steps),
            "clocks": clocks, "gpu_launches": launches}
+    if getattr(args, "stored", False):
+        st = prof["stored"]
+        gbs = st["bytes"] / (st["ms"] / 1e3) / 1e9
+        out["stored"] = {"ms_per_launch": st["ms"] / max(1, st["regions"]),
+                         "bytes_per_launch": st["bytes"] / max(1, st["regions"]),
+                         "achieved_gbs": gbs, "frac_hbm_peak": gbs / _hbm_peak(),
+                         "tflops": st["flops"] / (st["ms"] / 1e3) / 1e12}
     t.close()
     ctx.close()
     return out

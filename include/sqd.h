@@ -188,6 +188,52 @@ int sqd_diagonal(sqd_ctx *ctx, const sqd_tables *tables, double *d_diag);
 int sqd_sigma(sqd_ctx *ctx, sqd_tables *tables, const double *d_C,
               double *d_sigma, int nvec);
 
+/* ---------------------------------------------- SQD outer loop -- */
+
+/*
+ * Carry-over between SQD rounds (Section I: the diagonalisation also picks
+ * the configurations carried into the next round of the iterative loop).
+ *
+ * sqd_string_weights: d_wa[i] = sum_j C(i,j)^2 (n_alpha doubles) and
+ *   d_wb[j] = sum_i C(i,j)^2 (n_beta doubles) for the state d_C on the
+ *   table's sets (device buffers; either output may be NULL).
+ * sqd_select_strings: the strings d_str[i] with d_w[i] >= threshold, in
+ *   their order, into d_out (capacity n); *n_out (host) their count.  The
+ *   result, joined with newly sampled strings, is the raw input of the next
+ *   sqd_build_strings.
+ * sqd_map_vector: a warm-start guess for new sets from a state on old sets:
+ *   d_new_C(I', J') = d_old_C(I', J') if both strings are in the old sets,
+ *   else 0, normalised; *h_norm (host) receives the norm before
+ *   normalisation (0: no overlap, the vector is left zero).  All string sets
+ *   sorted ascending; vectors [n_alpha][n_beta] row-major on the device.
+ */
+int sqd_string_weights(sqd_ctx *ctx, const sqd_tables *tables, const double *d_C,
+                       double *d_wa, double *d_wb);
+int sqd_select_strings(sqd_ctx *ctx, const uint64_t *d_str, const double *d_w, int64_t n,
+                       double threshold, uint64_t *d_out, int64_t *n_out);
+int sqd_map_vector(sqd_ctx *ctx, const uint64_t *d_old_a, int64_t n_old_a,
+                   const uint64_t *d_old_b, int64_t n_old_b, const double *d_old_C,
+                   const uint64_t *d_new_a, int64_t n_new_a, const uint64_t *d_new_b,
+                   int64_t n_new_b, double *d_new_C, double *h_norm);
+
+/* ------------------------------------------------ stored-H variant -- */
+
+/*
+ * The paper's second method (Section II): compute the Hamiltonian once,
+ * store it, and re-use the stored elements in every iteration.
+ * sqd_stored_h_build assembles P H P as a CSR matrix held by the table
+ * object (12 bytes per nonzero: int32 column, FP64 value; rows in
+ * determinant order; per row the diagonal, alpha, beta and alpha-beta
+ * elements).  *nnz receives the nonzero count.  If the matrix would exceed
+ * max_bytes (0: no limit) or 90% of the free device memory it returns
+ * SQD_ENOMEM and builds nothing; N must be below 2^31.
+ * sqd_sigma_stored applies it: same contract as sqd_sigma.  Setting
+ * use_stored_h in sqd_options makes sqd_davidson use it.
+ */
+int sqd_stored_h_build(sqd_ctx *ctx, sqd_tables *tables, int64_t max_bytes, int64_t *nnz);
+int sqd_sigma_stored(sqd_ctx *ctx, sqd_tables *tables, const double *d_C, double *d_sigma,
+                     int nvec);
+
 /* ---------------------------------------------------- a8: Davidson -- */
 
 typedef struct {
@@ -198,7 +244,7 @@ typedef struct {
     double tol_residual; /* ||H x - theta x||_2 per root                       */
     double precond_floor;/* clamp of |theta - H_II| (e.g. 1e-8)                */
     int use_guess;       /* 1: d_C holds nroots initial vectors                */
-    int reserved;
+    int use_stored_h;    /* 1: apply the stored matrix (sqd_stored_h_build)    */
 } sqd_options;
 
 /*
@@ -288,7 +334,7 @@ int sqd_orbital_gradient(sqd_ctx *ctx, sqd_tables *tables, const double *d_rdm1,
  * on the context stream; 0 resets and stops timing.
  * Regions are booked in classes:
  *   0 same_spin_alpha, 1 same_spin_beta, 2 alpha_beta, 3 transpose,
- *   4 tables, 5 strings, 6 davidson, 7 rdm.
+ *   4 tables, 5 strings, 6 davidson, 7 rdm, 8 stored.
  * sqd_profile_read returns, for one class, the class name (static string),
  * the number of regions, their summed event time in ms, and the
  * algorithmic FP64 flops and compulsory bytes booked for them (host

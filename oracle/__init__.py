@@ -38,6 +38,7 @@ __all__ = [
     "lib", "build_strings", "hij", "dense_h", "sigma", "diag", "excitations",
     "string_energy", "expect", "rdm1", "rdm2", "energy_from_rdms",
     "orbital_gradient", "rotate_integrals", "davidson", "eigh_lowest",
+    "string_weights", "select_strings", "map_vector",
 ]
 
 _LIB = None
@@ -268,6 +269,41 @@ def rotate_integrals(h, V, U):
     h2 = U.T @ h @ U
     V2 = np.einsum("abcd,ap,bq,cr,ds->pqrs", V, U, U, U, U, optimize=True)
     return h2, V2
+
+
+# ------------------------------------------------------------ outer loop --
+
+def string_weights(C, na, nb):
+    """w_a[i] = sum_j C(i,j)^2, w_b[j] = sum_i C(i,j)^2 (probability of each
+    alpha / beta string in the state; the carry-over criterion of the SQD
+    loop, Section I)."""
+    M = np.asarray(C, dtype=np.float64).reshape(na, nb)
+    return (M * M).sum(axis=1), (M * M).sum(axis=0)
+
+
+def select_strings(s, w, threshold):
+    """The strings with weight >= threshold, in their order."""
+    return np.array([x for x, v in zip(np.asarray(s, np.uint64).tolist(), w) if v >= threshold],
+                    dtype=np.uint64)
+
+
+def map_vector(old_a, old_b, C, new_a, new_b):
+    """C' on the new sets: C'(I,J) = C(I,J) where both strings are in the old
+    sets, else 0, then normalised; returns (C', norm before normalisation)."""
+    ia = {int(x): i for i, x in enumerate(np.asarray(old_a, np.uint64).tolist())}
+    ib = {int(x): i for i, x in enumerate(np.asarray(old_b, np.uint64).tolist())}
+    M = np.asarray(C, dtype=np.float64).reshape(len(old_a), len(old_b))
+    out = np.zeros((len(new_a), len(new_b)))
+    for i, x in enumerate(np.asarray(new_a, np.uint64).tolist()):
+        if int(x) not in ia:
+            continue
+        for j, y in enumerate(np.asarray(new_b, np.uint64).tolist()):
+            if int(y) in ib:
+                out[i, j] = M[ia[int(x)], ib[int(y)]]
+    nrm = float(np.sqrt((out * out).sum()))
+    if nrm > 0:
+        out /= nrm
+    return out, nrm
 
 
 # ----------------------------------------------------------- eigensolvers --

@@ -25,7 +25,8 @@ __all__ = [
     "SQDError", "lib", "library_path", "Context", "Tables", "Options",
     "build_strings", "excitation_tables", "sigma", "davidson", "diagonal", "rdm",
     "orbital_gradient", "SQDEnergy", "davidson_batched", "batched_tuning",
-    "build_strings_noalloc",
+    "build_strings_noalloc", "stored_h_build", "sigma_stored", "string_weights",
+    "select_strings", "map_vector",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -47,10 +48,12 @@ EXPORTED = [
     "sqd_tables_export", "sqd_diagonal", "sqd_sigma", "sqd_davidson", "sqd_rdm",
     "sqd_profile_enable", "sqd_profile_read", "sqd_launch_count", "sqd_orbital_gradient",
     "sqd_build_strings_noalloc", "sqd_davidson_batched", "sqd_batched_tuning",
+    "sqd_stored_h_build", "sqd_sigma_stored", "sqd_string_weights", "sqd_select_strings",
+    "sqd_map_vector",
 ]
 
 PROFILE_CLASSES = ["same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose", "tables",
-                   "strings", "davidson", "rdm"]
+                   "strings", "davidson", "rdm", "stored"]
 
 
 class SQDError(RuntimeError):
@@ -64,7 +67,7 @@ class Options(ctypes.Structure):
     _fields_ = [("nroots", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("max_subspace", ctypes.c_int), ("tol_energy", ctypes.c_double),
                 ("tol_residual", ctypes.c_double), ("precond_floor", ctypes.c_double),
-                ("use_guess", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("use_guess", ctypes.c_int), ("use_stored_h", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -110,6 +113,12 @@ def lib():
     L.sqd_build_strings_noalloc.argtypes = [vp, vp, i64, i32, i32, vp, ctypes.POINTER(i64)]
     L.sqd_davidson_batched.argtypes = [vp, i32, vp, ctypes.POINTER(Options), vp, vp, vp, vp]
     L.sqd_batched_tuning.argtypes = [vp, ctypes.POINTER(dbl)]
+    L.sqd_stored_h_build.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
+    L.sqd_sigma_stored.argtypes = [vp, vp, vp, vp, i32]
+    L.sqd_string_weights.argtypes = [vp, vp, vp, vp, vp]
+    L.sqd_select_strings.argtypes = [vp, vp, vp, i64, dbl, vp, ctypes.POINTER(i64)]
+    L.sqd_map_vector.argtypes = [vp, vp, i64, vp, i64, vp, vp, i64, vp, i64, vp,
+                                 ctypes.POINTER(dbl)]
     _LIB = L
     return L
 
@@ -310,7 +319,7 @@ def sigma(ctx: Context, tables: Tables, C: torch.Tensor,
 def davidson(ctx: Context, tables: Tables, nroots: int = 1, tol_residual: float = 1e-8,
              tol_energy: float = 1e-8, max_iter: int = 200, max_subspace: int = 0,
              precond_floor: float = 1e-8, guess: Optional[torch.Tensor] = None,
-             raise_on_nonconvergence: bool = True):
+             raise_on_nonconvergence: bool = True, use_stored_h: bool = False):
     """sqd_davidson.  Returns (energies (numpy), C (nroots, n_alpha, n_beta)
     tensor, iterations, residual norms (numpy), status code)."""
     import numpy as np
@@ -322,7 +331,7 @@ def davidson(ctx: Context, tables: Tables, nroots: int = 1, tol_residual: float 
         use_guess = 1
     o = Options(nroots=nroots, max_iter=max_iter, max_subspace=max_subspace,
                 tol_energy=tol_energy, tol_residual=tol_residual, precond_floor=precond_floor,
-                use_guess=use_guess, reserved=0)
+                use_guess=use_guess, use_stored_h=1 if use_stored_h else 0)
     e = np.zeros(nroots)
     r = np.zeros(nroots)
     it = ctypes.c_int(0)
@@ -347,7 +356,8 @@ def davidson_batched(ctx: Context, tables, tol_residual: float = 1e-8,
           for t in tables] if want_vectors else None
     ptrs = (ctypes.c_void_p * nb)(*([c.data_ptr() for c in Cs] if Cs else [0] * nb))
     o = Options(nroots=1, max_iter=max_iter, max_subspace=max_subspace, tol_energy=tol_energy,
-                tol_residual=tol_residual, precond_floor=precond_floor, use_guess=0, reserved=0)
+                tol_residual=tol_residual, precond_floor=precond_floor, use_guess=0,
+                use_stored_h=0)
     e = np.zeros(nb)
     it = np.zeros(nb, dtype=np.int32)
     st = np.zeros(nb, dtype=np.int32)
@@ -357,6 +367,66 @@ def davidson_batched(ctx: Context, tables, tol_residual: float = 1e-8,
         ptrs if Cs else None, ctypes.c_void_p(it.ctypes.data), ctypes.c_void_p(st.ctypes.data)),
         allow=allow)
     return e, Cs, it, st, rc
+
+
+def stored_h_build(ctx: Context, tables: Tables, max_bytes: int = 0) -> int:
+    """sqd_stored_h_build: assemble P H P once (the stored-H method); returns
+    the nonzero count.  Raises SQDError(SQD_ENOMEM) if it would not fit."""
+    n = ctypes.c_int64()
+    ctx._check(ctx._lib.sqd_stored_h_build(ctx.handle, tables.handle, int(max_bytes),
+                                           ctypes.byref(n)))
+    return n.value
+
+
+def sigma_stored(ctx: Context, tables: Tables, C: torch.Tensor,
+                 out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """sqd_sigma_stored: sigma = H C with the stored matrix."""
+    _need_cuda(C, "C", torch.float64)
+    nvec = C.numel() // tables.ndet
+    if out is None:
+        out = torch.empty_like(C)
+    ctx._check(ctx._lib.sqd_sigma_stored(ctx.handle, tables.handle, _ptr(C), _ptr(out), nvec))
+    return out
+
+
+def string_weights(ctx: Context, tables: Tables, C: torch.Tensor):
+    """sqd_string_weights: (w_alpha, w_beta), the squared-norm weight of every
+    alpha and beta string in the state C."""
+    _need_cuda(C, "C", torch.float64)
+    dev = "cuda:%d" % ctx.device
+    wa = torch.empty(tables.na, dtype=torch.float64, device=dev)
+    wb = torch.empty(tables.nb, dtype=torch.float64, device=dev)
+    ctx._check(ctx._lib.sqd_string_weights(ctx.handle, tables.handle, _ptr(C), _ptr(wa), _ptr(wb)))
+    return wa, wb
+
+
+def select_strings(ctx: Context, strings: torch.Tensor, weights: torch.Tensor,
+                   threshold: float) -> torch.Tensor:
+    """sqd_select_strings: the strings whose weight is >= threshold."""
+    _need_cuda(strings, "strings", torch.int64)
+    _need_cuda(weights, "weights", torch.float64)
+    out = torch.empty_like(strings)
+    n = ctypes.c_int64()
+    ctx._check(ctx._lib.sqd_select_strings(ctx.handle, _ptr(strings), _ptr(weights),
+                                           strings.numel(), float(threshold), _ptr(out),
+                                           ctypes.byref(n)))
+    return out[:n.value]
+
+
+def map_vector(ctx: Context, old_a: torch.Tensor, old_b: torch.Tensor, C: torch.Tensor,
+               new_a: torch.Tensor, new_b: torch.Tensor):
+    """sqd_map_vector: warm-start guess on (new_a, new_b) from the state C on
+    (old_a, old_b).  Returns (vector (n_new_a, n_new_b), norm before
+    normalisation)."""
+    for x, nm in ((old_a, "old_a"), (old_b, "old_b"), (new_a, "new_a"), (new_b, "new_b")):
+        _need_cuda(x, nm, torch.int64)
+    _need_cuda(C, "C", torch.float64)
+    out = torch.empty((new_a.numel(), new_b.numel()), dtype=torch.float64, device=C.device)
+    nrm = ctypes.c_double()
+    ctx._check(ctx._lib.sqd_map_vector(ctx.handle, _ptr(old_a), old_a.numel(), _ptr(old_b),
+                                       old_b.numel(), _ptr(C), _ptr(new_a), new_a.numel(),
+                                       _ptr(new_b), new_b.numel(), _ptr(out), ctypes.byref(nrm)))
+    return out, nrm.value
 
 
 def batched_tuning(ctx: Context) -> float:

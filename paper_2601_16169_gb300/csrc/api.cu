@@ -146,7 +146,7 @@ void sqd_destroy(sqd_ctx *ctx) {
 
 static const char *k_prof_names[PROF_NCLASS] = {
     "same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose",
-    "tables",          "strings",        "davidson",   "rdm"};
+    "tables",          "strings",        "davidson",   "rdm", "stored"};
 
 int sqd_profile_enable(sqd_ctx *ctx, int enable) {
     if (!ctx) return fail_noctx(SQD_EINVAL, "sqd_profile_enable: ctx is NULL");
@@ -414,7 +414,8 @@ void sqd_free_tables(sqd_tables *t) {
     if (!t->shared) free_spin(&t->b_own);
     void *ptrs[] = {t->h,         t->V,          t->diag,       t->ab.chunk_rows,
                     t->ab.group_rows, t->scratch_t, t->scratch_s, t->rdm_iket,
-                    t->rdm_ibra,  t->rdm_ipq,    t->rdm_chunks, t->rdm_groups};
+                    t->rdm_ibra,  t->rdm_ipq,    t->rdm_chunks, t->rdm_groups,
+                    t->st_rowptr, t->st_col,     t->st_val};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete t;
@@ -634,7 +635,13 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
         SQD_TRY(launch_set_unit(ctx, w.Vb, N, k, w.idx));
         m = k;
     }
-    SQD_TRY(sigma_impl(ctx, t, w.Vb, w.Wb, m));
+    auto apply_h = [&](const double *Cin, double *Sout, int nv) -> int {
+        if (o->use_stored_h) return stored_sigma(ctx, t, Cin, Sout, nv);
+        return sigma_impl(ctx, t, Cin, Sout, nv);
+    };
+    if (o->use_stored_h && !t->st_rowptr)
+        return sqd_fail(ctx, SQD_EINVAL, "use_stored_h set but sqd_stored_h_build was not called");
+    SQD_TRY(apply_h(w.Vb, w.Wb, m));
     for (int j = 0; j < m; j++) SQD_TRY(dot_col(j + 1, j));
 
     std::vector<double> theta(M), theta_old(k, INFINITY), rn2(k), rn(k);
@@ -714,8 +721,7 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
             if (!res_ok) status = SQD_EBREAKDOWN;
             break;
         }
-        SQD_TRY(sigma_impl(ctx, t, w.Vb + (int64_t)m_old * N, w.Wb + (int64_t)m_old * N,
-                           m - m_old));
+        SQD_TRY(apply_h(w.Vb + (int64_t)m_old * N, w.Wb + (int64_t)m_old * N, m - m_old));
         for (int j = m_old; j < m; j++) SQD_TRY(dot_col(j + 1, j));
     }
     // outputs: Ritz vectors with the phase fixed, energies, residuals
@@ -746,6 +752,53 @@ int sqd_davidson(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, double *h_en
         return sqd_fail(ctx, SQD_EINVAL, "invalid Davidson options");
     SQD_TRY(use_device(ctx));
     return davidson_impl(ctx, t, o, h_energies, d_C, h_iters, h_res);
+}
+
+int sqd_string_weights(sqd_ctx *ctx, const sqd_tables *t, const double *d_C, double *d_wa,
+                       double *d_wb) {
+    if (!ctx || !t) return fail_noctx(SQD_EINVAL, "sqd_string_weights: NULL argument");
+    if (!d_C || (!d_wa && !d_wb)) return sqd_fail(ctx, SQD_EINVAL, "NULL buffer");
+    SQD_TRY(use_device(ctx));
+    return launch_string_weights(ctx, d_C, t->a.n, t->b->n, d_wa, d_wb);
+}
+
+int sqd_select_strings(sqd_ctx *ctx, const uint64_t *d_str, const double *d_w, int64_t n,
+                       double threshold, uint64_t *d_out, int64_t *n_out) {
+    if (!ctx) return fail_noctx(SQD_EINVAL, "sqd_select_strings: NULL context");
+    if (!n_out || n < 0 || (n > 0 && (!d_str || !d_w || !d_out)))
+        return sqd_fail(ctx, SQD_EINVAL, "bad arguments");
+    if (!std::isfinite(threshold)) return sqd_fail(ctx, SQD_EINVAL, "threshold not finite");
+    SQD_TRY(use_device(ctx));
+    return launch_select_strings(ctx, d_str, d_w, n, threshold, d_out, n_out);
+}
+
+int sqd_map_vector(sqd_ctx *ctx, const uint64_t *d_old_a, int64_t n_old_a,
+                   const uint64_t *d_old_b, int64_t n_old_b, const double *d_old_C,
+                   const uint64_t *d_new_a, int64_t n_new_a, const uint64_t *d_new_b,
+                   int64_t n_new_b, double *d_new_C, double *h_norm) {
+    if (!ctx) return fail_noctx(SQD_EINVAL, "sqd_map_vector: NULL context");
+    if (n_old_a < 1 || n_old_b < 1 || n_new_a < 1 || n_new_b < 1 || !d_old_a || !d_old_b ||
+        !d_old_C || !d_new_a || !d_new_b || !d_new_C || !h_norm)
+        return sqd_fail(ctx, SQD_EINVAL, "bad arguments");
+    SQD_TRY(use_device(ctx));
+    return launch_map_vector(ctx, d_old_a, n_old_a, d_old_b, n_old_b, d_old_C, d_new_a, n_new_a,
+                             d_new_b, n_new_b, d_new_C, h_norm);
+}
+
+int sqd_stored_h_build(sqd_ctx *ctx, sqd_tables *t, int64_t max_bytes, int64_t *nnz) {
+    if (!ctx || !t || !nnz) return fail_noctx(SQD_EINVAL, "sqd_stored_h_build: NULL argument");
+    SQD_TRY(use_device(ctx));
+    return stored_build(ctx, t, max_bytes, nnz);
+}
+
+int sqd_sigma_stored(sqd_ctx *ctx, sqd_tables *t, const double *d_C, double *d_sigma,
+                     int nvec) {
+    if (!ctx || !t) return fail_noctx(SQD_EINVAL, "sqd_sigma_stored: NULL argument");
+    if (!t->st_rowptr) return sqd_fail(ctx, SQD_EINVAL, "sqd_stored_h_build was not called");
+    if (nvec < 1 || !d_C || !d_sigma || d_C == d_sigma)
+        return sqd_fail(ctx, SQD_EINVAL, "bad vectors");
+    SQD_TRY(use_device(ctx));
+    return stored_sigma(ctx, t, d_C, d_sigma, nvec);
 }
 
 int sqd_davidson_batched(sqd_ctx *ctx, int nbatch, sqd_tables *const *tables,

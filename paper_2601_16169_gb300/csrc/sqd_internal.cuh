@@ -19,6 +19,7 @@ enum prof_class {
     PROF_STRINGS,         // string filtering, sort, scan
     PROF_DAVIDSON,        // Davidson vector kernels and the Jacobi solver
     PROF_RDM,             // density matrices
+    PROF_STORED,          // stored-H sparse matrix-vector product
     PROF_NCLASS
 };
 
@@ -111,6 +112,11 @@ struct sqd_tables {
     uint32_t *rdm_ipq = nullptr;
     int rdm_nchunks = 0, rdm_ngroups = 0;
     int64_t *rdm_chunks = nullptr, *rdm_groups = nullptr;
+    // stored-H CSR (built on request)
+    int64_t st_nnz = 0;
+    int64_t *st_rowptr = nullptr;
+    int32_t *st_col = nullptr;
+    double *st_val = nullptr;
     int64_t bytes = 0;
 };
 
@@ -204,6 +210,19 @@ int launch_fix_phase(sqd_ctx *, double *X, int64_t ld, int k, int64_t n, double 
 int launch_gdk_basis(sqd_ctx *, const double *Y, int m, int m2, const double *P, int mp, int k,
                      int ldp, double *Z, int ldz, int *r_dev);
 int launch_identity_cols(sqd_ctx *, double *Y, int r, int k, int ld);
+
+// outer loop
+int launch_string_weights(sqd_ctx *, const double *C, int64_t na, int64_t nb, double *wa,
+                          double *wb);
+int launch_select_strings(sqd_ctx *, const uint64_t *s, const double *w, int64_t n, double thr,
+                          uint64_t *out, int64_t *n_out);
+int launch_map_vector(sqd_ctx *, const uint64_t *oa, int64_t noa, const uint64_t *ob, int64_t nob,
+                      const double *Cold, const uint64_t *nas, int64_t nna, const uint64_t *nbs,
+                      int64_t nnb, double *Cnew, double *norm_out);
+
+// stored H
+int stored_build(sqd_ctx *ctx, sqd_tables *t, int64_t max_bytes, int64_t *nnz_out);
+int stored_sigma(sqd_ctx *ctx, const sqd_tables *t, const double *C, double *S, int nvec);
 
 // batched
 int davidson_batched_impl(sqd_ctx *ctx, int nprob, sqd_tables *const *tables,

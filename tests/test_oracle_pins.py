@@ -405,3 +405,35 @@ def test_orbital_gradient_vanishes_at_full_ci():
     g = oracle.orbital_gradient(h, V, oracle.rdm1(norb, sa, sb, c),
                                 oracle.rdm2(norb, sa, sb, c))
     assert np.max(np.abs(g)) <= 1e-10
+
+
+# ------------------------------------------------------------ outer loop ---
+
+def test_outer_loop_helpers_invariants():
+    rng = np.random.default_rng(12)
+    sa = _rand_strings(rng, 8, 3, 20)
+    sb = _rand_strings(rng, 8, 2, 15)
+    C = rng.normal(size=len(sa) * len(sb))
+    wa, wb = oracle.string_weights(C, len(sa), len(sb))
+    assert abs(wa.sum() - C @ C) <= 1e-12 and abs(wb.sum() - C @ C) <= 1e-12
+    # mapping onto the same sets is normalisation
+    M, nrm = oracle.map_vector(sa, sb, C, sa, sb)
+    assert abs(nrm - np.linalg.norm(C)) <= 1e-12
+    assert np.allclose(M.reshape(-1), C / np.linalg.norm(C), atol=1e-15)
+    # onto a superset: old values kept in place, zeros elsewhere; and back
+    full_a, full_b = si.full_strings(8, 3), si.full_strings(8, 2)
+    M2, _ = oracle.map_vector(sa, sb, C, full_a, full_b)
+    ia = np.searchsorted(full_a, sa)
+    ib = np.searchsorted(full_b, sb)
+    assert np.count_nonzero(M2) == np.count_nonzero(C)
+    assert np.allclose(M2[np.ix_(ia, ib)].reshape(-1), C / np.linalg.norm(C))
+    back, _ = oracle.map_vector(full_a, full_b, M2, sa, sb)
+    assert np.allclose(back.reshape(-1), C / np.linalg.norm(C))
+    # disjoint sets: nothing carried
+    other = np.setdiff1d(full_a, sa)
+    Z, z = oracle.map_vector(sa, sb, C, other, sb)
+    assert z == 0.0 and not Z.any()
+    assert len(oracle.select_strings(sa, wa, -1.0)) == len(sa)
+    assert len(oracle.select_strings(sa, wa, wa.max() + 1)) == 0
+    keep = oracle.select_strings(sa, wa, np.median(wa))
+    assert set(keep.tolist()) == {int(x) for x, v in zip(sa, wa) if v >= np.median(wa)}
