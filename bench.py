@@ -157,11 +157,28 @@ def default_cpu_rows(name):
     return {"scale36": 400000, "h2o29": 4000000, "adjoint29": 2000000, "full8": 4900}[name]
 
 
+# ------------------------------------------------------ replica timing ---
+
+def aggregate_replicas(dev_ms, e2e_s, work, world, device=None):
+    """Replicas-only multi-GPU: every rank solves its own copy of the
+    workload.  Returns (max device ms, max e2e seconds, total work over
+    ranks); with world == 1 the inputs unchanged."""
+    if world <= 1:
+        return dev_ms, e2e_s, work
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([dev_ms, e2e_s], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    cnt = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    dist.all_reduce(cnt)
+    return float(tt[0]), float(tt[1]), float(cnt[0])
+
+
 # ------------------------------------------------------------ ours -------
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("k_sigma.cu",):
+    for f in ("k_sigma.cu", "sigma_body.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2601_16169_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -250,17 +267,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_s = time.perf_counter() - t0
 
     # aggregate over ranks: total work / max time
-    t_max = dev_ms
-    hc_tot = hc
-    if world > 1:
-        tt = torch.tensor([dev_ms, e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max, e2e_max = float(tt[0]), float(tt[1])
-        cnt = torch.tensor([hc], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(cnt)
-        hc_tot = float(cnt[0])
-    else:
-        e2e_max = e2e_s
+    t_max, e2e_max, hc_tot = aggregate_replicas(dev_ms, e2e_s, hc, world, dev)
     if rank != 0:
         return None
 
