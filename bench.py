@@ -78,6 +78,8 @@ def _args():
                         "batched: the 64-subspace workload in one batched solve vs one "
                         "solve per subspace")
     p.add_argument("--nbatch", type=int, default=64)
+    p.add_argument("--sigma-mode", type=int, default=0, choices=[0, 1],
+                   help="0: native FP64 sigma (headline); 1: double-float on the FP32 pipe")
     p.add_argument("--stored", action="store_true",
                    help="sigma mode: apply the stored H (sparse matrix) instead")
     return p.parse_args()
@@ -222,6 +224,8 @@ def run_ours(args, rank, world, local_rank):
     def step(raw, h, V):
         s = sqd.build_strings(ctx, raw, w.norb, w.nelec_a)
         t = sqd.excitation_tables(ctx, w.norb, s, w.nelec_a, s, w.nelec_b, h, V, 0.0)
+        if args.sigma_mode:
+            t.set_sigma_mode(args.sigma_mode)
         e, C, it, res, rc = sqd.davidson(ctx, t, **opts)
         t.close()
         del C
@@ -335,6 +339,12 @@ def run_ours(args, rank, world, local_rank):
         line["sigma_only"]["workload"] = DESCR[args.sigma_extra]
         line["sigma_only"]["det_per_s"] = \
             ex["value"] * ex["tables"]["n_alpha"] * ex["tables"]["n_beta"]
+        # the same sigma with the double-float products (opt-in mode 1)
+        a3 = argparse.Namespace(**vars(a2))
+        a3.sigma_mode = 1
+        ex = run_sigma_only(a3, rank, world, local_rank)
+        line["sigma_only_df32"] = {k: ex[k] for k in ("value", "unit", "ms_per_step", "kernels",
+                                                      "clocks")}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_rows or default_cpu_rows(args.workload))
     return line
@@ -359,6 +369,8 @@ def run_sigma_only(args, rank, world, local_rank):
         w.strings_a.size, w.strings_b.size)).to(dev)
     S = torch.empty_like(C)
     apply = sqd.sigma
+    if getattr(args, "sigma_mode", 0):
+        t.set_sigma_mode(args.sigma_mode)
     if getattr(args, "stored", False):
         sqd.stored_h_build(ctx, t)
         apply = sqd.sigma_stored
@@ -382,7 +394,7 @@ def run_sigma_only(args, rank, world, local_rank):
     if rank != 0:
         return None
     sig = {k: prof[k] for k in ("same_spin_alpha", "same_spin_beta", "alpha_beta")}
-    out = {"mode": "sigma", "metric": METRIC, "value": args.steps / (ms / 1e3), "unit": UNIT,
+    out = {"mode": "sigma", "sigma_mode": getattr(args, "sigma_mode", 0), "metric": METRIC, "value": args.steps / (ms / 1e3), "unit": UNIT,
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms / args.steps, "higher_is_better": True, "dtype": "f64",
            "config": {"workload": DESCR[args.workload]}, "tables": t.info(),

@@ -216,6 +216,22 @@ int sqd_map_vector(sqd_ctx *ctx, const uint64_t *d_old_a, int64_t n_old_a,
                    const uint64_t *d_new_a, int64_t n_new_a, const uint64_t *d_new_b,
                    int64_t n_new_b, double *d_new_C, double *h_norm);
 
+/*
+ * Arithmetic of the sigma products of one table object:
+ *   mode 0 (default): native FP64 multiply-adds;
+ *   mode 1: double-float -- every FP64 operand split into a pair of floats
+ *     (48 of 53 bits), products formed exactly (Dekker) and summed
+ *     error-free (Knuth TwoSum) on the FP32 pipe, results in FP64.  Relative
+ *     error of a few 2^-48 per term; sigma agrees with mode 0 to ~1e-14.
+ *     Not in the paper: GB300's FP32 pipe is ~58x its FP64 pipe, and the
+ *     sigma terms are FP64-bound.
+ * Applies to sqd_sigma and sqd_davidson on these tables (not to the batched
+ * solver, the stored-H product or the RDMs, which stay FP64).
+ * Mode 1 makes float-pair copies of the coefficient tables and the
+ * diagonal on first use (the same bytes again) plus one scratch vector.
+ */
+int sqd_tables_set_sigma_mode(sqd_tables *tables, int mode);
+
 /* ------------------------------------------------ stored-H variant -- */
 
 /*

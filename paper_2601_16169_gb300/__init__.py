@@ -49,7 +49,7 @@ EXPORTED = [
     "sqd_profile_enable", "sqd_profile_read", "sqd_launch_count", "sqd_orbital_gradient",
     "sqd_build_strings_noalloc", "sqd_davidson_batched", "sqd_batched_tuning",
     "sqd_stored_h_build", "sqd_sigma_stored", "sqd_string_weights", "sqd_select_strings",
-    "sqd_map_vector",
+    "sqd_map_vector", "sqd_tables_set_sigma_mode",
 ]
 
 PROFILE_CLASSES = ["same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose", "tables",
@@ -119,6 +119,7 @@ def lib():
     L.sqd_select_strings.argtypes = [vp, vp, vp, i64, dbl, vp, ctypes.POINTER(i64)]
     L.sqd_map_vector.argtypes = [vp, vp, i64, vp, i64, vp, vp, i64, vp, i64, vp,
                                  ctypes.POINTER(dbl)]
+    L.sqd_tables_set_sigma_mode.argtypes = [vp, i32]
     _LIB = L
     return L
 
@@ -217,6 +218,11 @@ class Tables:
         keys = ["norb", "n_alpha", "n_beta", "nnz1_alpha", "nnz2_alpha", "nnz1_beta",
                 "nnz2_beta", "shared", "device_bytes", "max_singles", "max_doubles"]
         return {k: int(buf[i]) for i, k in enumerate(keys)}
+
+    def set_sigma_mode(self, mode: int):
+        """sqd_tables_set_sigma_mode: 0 native FP64, 1 double-float on the
+        FP32 pipe (sigma and Davidson on these tables)."""
+        self.ctx._check(self.ctx._lib.sqd_tables_set_sigma_mode(self.handle, int(mode)))
 
     def export(self, spin: int, kind: int) -> dict:
         """Host (numpy) copy of one excitation table: off, tgt, orb, sign, val."""

@@ -234,8 +234,9 @@ int sqd_build_strings(sqd_ctx *ctx, const uint64_t *d_raw, int64_t n_raw, int no
 // ----------------------------------------------------------- a2-a4 ------
 
 static void free_spin(spin_tables *s) {
-    void *ptrs[] = {s->str,  s->off1, s->tgt1, s->pq1,  s->sgn1,   s->val1, s->off2,
-                    s->tgt2, s->orb2, s->sgn2, s->val2, s->energy, s->W,    s->u};
+    void *ptrs[] = {s->str,  s->off1, s->tgt1,   s->pq1, s->sgn1, s->val1,  s->off2,
+                    s->tgt2, s->orb2, s->sgn2,   s->val2, s->energy, s->W, s->u,
+                    s->val1f, s->val2f, s->Wf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     *s = spin_tables();
@@ -415,10 +416,18 @@ void sqd_free_tables(sqd_tables *t) {
     void *ptrs[] = {t->h,         t->V,          t->diag,       t->ab.chunk_rows,
                     t->ab.group_rows, t->scratch_t, t->scratch_s, t->rdm_iket,
                     t->rdm_ibra,  t->rdm_ipq,    t->rdm_chunks, t->rdm_groups,
-                    t->st_rowptr, t->st_col,     t->st_val};
+                    t->st_rowptr, t->st_col,     t->st_val,  t->Vf,
+                    t->diagf,     t->scratch_c};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete t;
+}
+
+int sqd_tables_set_sigma_mode(sqd_tables *t, int mode) {
+    if (!t) return fail_noctx(SQD_EINVAL, "sqd_tables_set_sigma_mode: tables is NULL");
+    if (mode != 0 && mode != 1) return fail_noctx(SQD_EINVAL, "sigma mode must be 0 or 1");
+    t->sigma_mode = mode;
+    return SQD_OK;
 }
 
 int sqd_tables_info(const sqd_tables *t, int64_t *info) {
@@ -518,6 +527,12 @@ static int sigma_impl(sqd_ctx *ctx, sqd_tables *t, const double *C, double *S, i
     double f_a, f_b, f_ab;
     sigma_work(t, &f_a, &f_b, &f_ab);
     SQD_TRY(ensure_scratch(ctx, t));
+    if (t->sigma_mode == 1) {
+        SQD_TRY(df_prepare(ctx, t));
+        for (int v = 0; v < nvec; v++)
+            SQD_TRY(sigma_df_one(ctx, t, C + (int64_t)v * N, S + (int64_t)v * N, f_a, f_b, f_ab));
+        return SQD_OK;
+    }
     for (int v = 0; v < nvec; v++) {
         const double *Cv = C + (int64_t)v * N;
         double *Sv = S + (int64_t)v * N;

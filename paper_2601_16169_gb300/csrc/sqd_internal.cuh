@@ -79,6 +79,9 @@ struct spin_tables {
 
     std::vector<int64_t> h_off1;  // host copy of off1 (scheduling)
     int64_t max1 = 0, max2 = 0;
+
+    // float-pair copies for the double-float sigma mode (made on first use)
+    float2 *val1f = nullptr, *val2f = nullptr, *Wf = nullptr;
 };
 
 // Work decomposition of the alpha-beta (paired singles) kernel.
@@ -112,6 +115,11 @@ struct sqd_tables {
     uint32_t *rdm_ipq = nullptr;
     int rdm_nchunks = 0, rdm_ngroups = 0;
     int64_t *rdm_chunks = nullptr, *rdm_groups = nullptr;
+    // double-float sigma mode (0: FP64, 1: df32)
+    int sigma_mode = 0;
+    bool df_ready = false;
+    float2 *Vf = nullptr, *diagf = nullptr;
+    double *scratch_c = nullptr;  // C as float pairs (8 bytes per element)
     // stored-H CSR (built on request)
     int64_t st_nnz = 0;
     int64_t *st_rowptr = nullptr;
@@ -210,6 +218,11 @@ int launch_fix_phase(sqd_ctx *, double *X, int64_t ld, int k, int64_t n, double 
 int launch_gdk_basis(sqd_ctx *, const double *Y, int m, int m2, const double *P, int mp, int k,
                      int ldp, double *Z, int ldz, int *r_dev);
 int launch_identity_cols(sqd_ctx *, double *Y, int r, int k, int ld);
+
+// double-float sigma
+int df_prepare(sqd_ctx *ctx, sqd_tables *t);
+int sigma_df_one(sqd_ctx *ctx, sqd_tables *t, const double *Cv, double *Sv, double f_a,
+                 double f_b, double f_ab);
 
 // outer loop
 int launch_string_weights(sqd_ctx *, const double *C, int64_t na, int64_t nb, double *wa,
