@@ -38,7 +38,7 @@ UNIT = "H·C/s"
 
 # Davidson settings per workload (convergence readings of the build)
 SOLVE = {
-    "scale36": dict(nroots=1, tol_residual=1e-5, tol_energy=1e-8, max_iter=200),
+    "scale36": dict(nroots=1, tol_residual=1e-5, tol_energy=1e-8, max_iter=400),
     "h2o29": dict(nroots=8, tol_residual=1e-8, tol_energy=1e-8, max_iter=200),
     "adjoint29": dict(nroots=1, tol_residual=1e-5, tol_energy=1e-8, max_iter=200),
     "full8": dict(nroots=1, tol_residual=1e-8, tol_energy=1e-10, max_iter=200),
@@ -72,14 +72,17 @@ def _args():
     p.add_argument("--cpu-rows", type=int, default=None,
                    help="rows of sigma in the CPU-baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mode", default="solve", choices=["solve", "sigma", "batched"],
+    p.add_argument("--mode", default="solve", choices=["solve", "sigma", "batched", "adjoint"],
                    help="solve: the whole path per step; sigma: one sigma = H C per step "
                         "on prebuilt tables (kernel-only number, used for profiling); "
                         "batched: the 64-subspace workload in one batched solve vs one "
-                        "solve per subspace")
+                        "solve per subspace; adjoint: the backward pass (RDMs + orbital "
+                        "gradient) of a converged state against one sigma")
     p.add_argument("--nbatch", type=int, default=64)
     p.add_argument("--sigma-mode", type=int, default=0, choices=[0, 1],
                    help="0: native FP64 sigma (headline); 1: double-float on the FP32 pipe")
+    p.add_argument("--max-subspace", type=int, default=None,
+                   help="Davidson subspace limit (default max(8 nroots, 16))")
     p.add_argument("--stored", action="store_true",
                    help="sigma mode: apply the stored H (sparse matrix) instead")
     return p.parse_args()
@@ -211,7 +214,9 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     w = si.workload(args.workload)
-    opts = SOLVE[args.workload]
+    opts = dict(SOLVE[args.workload])
+    if args.max_subspace:
+        opts["max_subspace"] = args.max_subspace
     ctx = sqd.Context(local_rank)
     stream = torch.cuda.current_stream(dev)
 
@@ -303,7 +308,9 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": DESCR[args.workload],
                    "l2": "inputs larger than L2 (3.2 GB vectors)" if w.ndet > 2e7 else
                    "vectors may fit in L2",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "davidson": opts,
+                   "sigma_mode": "double-float (FP32 pipe)" if args.sigma_mode else "fp64"},
         "time_to_converged_E_s": t_max / 1e3 / args.steps,
         "davidson_iterations": int(res_last[1]),
         "energy": float(res_last[0][0]),
@@ -500,6 +507,75 @@ def run_batched(args, rank, world, local_rank):
     return out
 
 
+def run_adjoint(args, rank, world, local_rank):
+    """Backward pass of E(h, V) on a converged ground state: one step is the
+    spin-summed 1-RDM and 2-RDM of C (dE/dh, 2 dE/dV) plus the orbital
+    gradient, timed against one sigma = H C on the same tables."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2601_16169_gb300 as sqd
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    name = args.workload if args.workload != "h2o29" else "adjoint29"
+    w = si.workload(name)
+    ctx = sqd.Context(local_rank)
+    s = sqd.build_strings(ctx, torch.from_numpy(w.raw_a.view(np.int64).copy()).to(dev),
+                          w.norb, w.nelec_a)
+    t = sqd.excitation_tables(ctx, w.norb, s, w.nelec_a, s, w.nelec_b,
+                              torch.from_numpy(w.h).to(dev), torch.from_numpy(w.V).to(dev), 0.0)
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    e, X, iters, res, rc = sqd.davidson(ctx, t, **SOLVE[name])
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    solve_ms = ev0.elapsed_time(ev1)
+    C = X[0].contiguous()
+    S = torch.empty_like(C)
+
+    def backward():
+        g1, g2 = sqd.rdm(ctx, t, C)
+        return sqd.orbital_gradient(ctx, t, g1, g2)
+
+    def timed(fn, profile=False):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        if profile:
+            ctx.profile(True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        return ev0.elapsed_time(ev1) / args.steps
+
+    clk = ClockSampler(local_rank)
+    clk.start()
+    sigma_ms = timed(lambda: sqd.sigma(ctx, t, C, S))
+    back_ms = timed(backward, profile=True)
+    prof = ctx.profile_read()
+    clocks = clk.stop()
+    launches = ctx.launch_count()
+    if rank != 0:
+        return None
+    out = {"mode": "adjoint", "metric": METRIC,
+           "value": 1e3 / back_ms, "unit": "backward passes/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": back_ms,
+           "higher_is_better": True, "dtype": "f64",
+           "config": {"workload": DESCR[name] + "; backward = 1-RDM + 2-RDM + orbital gradient"},
+           "tables": t.info(), "backward_ms": back_ms, "sigma_ms": sigma_ms,
+           "backward_over_sigma": back_ms / sigma_ms, "forward_solve_ms": solve_ms,
+           "forward_iterations": int(iters), "energy": float(e[0]),
+           "rdm_kernel_ms": prof["rdm"]["ms"] / max(1, args.steps),
+           "clocks": clocks, "gpu_launches": launches}
+    t.close()
+    ctx.close()
+    return out
+
+
 def _hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -556,6 +632,8 @@ def main():
         line = run_sigma_only(args, rank, world, local_rank)
     elif args.mode == "batched":
         line = run_batched(args, rank, world, local_rank)
+    elif args.mode == "adjoint":
+        line = run_adjoint(args, rank, world, local_rank)
     else:
         line = run_ours(args, rank, world, local_rank)
     if line is not None:

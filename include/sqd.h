@@ -350,7 +350,10 @@ int sqd_orbital_gradient(sqd_ctx *ctx, sqd_tables *tables, const double *d_rdm1,
  * on the context stream; 0 resets and stops timing.
  * Regions are booked in classes:
  *   0 same_spin_alpha, 1 same_spin_beta, 2 alpha_beta, 3 transpose,
- *   4 tables, 5 strings, 6 davidson, 7 rdm, 8 stored.
+ *   4 tables, 5 strings, 6 davidson (Ritz vectors, residuals,
+ *   preconditioner, restart), 7 rdm, 8 stored, 9 ortho (Davidson
+ *   Gram-Schmidt and projected-matrix columns), 10 eigh (Rayleigh-Ritz
+ *   eigensolver).
  * sqd_profile_read returns, for one class, the class name (static string),
  * the number of regions, their summed event time in ms, and the
  * algorithmic FP64 flops and compulsory bytes booked for them (host

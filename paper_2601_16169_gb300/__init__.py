@@ -53,7 +53,7 @@ EXPORTED = [
 ]
 
 PROFILE_CLASSES = ["same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose", "tables",
-                   "strings", "davidson", "rdm", "stored"]
+                   "strings", "davidson", "rdm", "stored", "ortho", "eigh"]
 
 
 class SQDError(RuntimeError):

@@ -146,7 +146,8 @@ void sqd_destroy(sqd_ctx *ctx) {
 
 static const char *k_prof_names[PROF_NCLASS] = {
     "same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose",
-    "tables",          "strings",        "davidson",   "rdm", "stored"};
+    "tables",          "strings",        "davidson",   "rdm", "stored",
+    "ortho",           "eigh"};
 
 int sqd_profile_enable(sqd_ctx *ctx, int enable) {
     if (!ctx) return fail_noctx(SQD_EINVAL, "sqd_profile_enable: ctx is NULL");
@@ -572,16 +573,27 @@ int sqd_sigma(sqd_ctx *ctx, sqd_tables *t, const double *d_C, double *d_sigma, i
 struct dav_work {
     double *Vb = nullptr, *Wb = nullptr, *X = nullptr, *R = nullptr, *Tmp = nullptr;
     double *G = nullptr, *evals = nullptr, *evecs = nullptr, *dots = nullptr, *partial = nullptr;
-    double *phase = nullptr, *Yprev = nullptr, *Z = nullptr;
+    double *phase = nullptr, *Yprev = nullptr, *Z = nullptr, *P = nullptr, *GZ = nullptr;
+    double *tn2 = nullptr;
     int64_t *idx = nullptr;
     int *rdev = nullptr;
     ~dav_work() {
-        void *p[] = {Vb, Wb, X, R, Tmp, G, evals, evecs, dots, partial, phase, idx, Yprev, Z, rdev};
+        void *p[] = {Vb, Wb, X, R, Tmp, G, evals, evecs, dots, partial, phase, idx, Yprev, Z, P,
+                     GZ, tn2, rdev};
         for (void *q : p)
             if (q) cudaFree(q);
     }
 };
 
+// Block Davidson with GD+k restart.  Per iteration: Rayleigh-Ritz on the
+// projected matrix G = V^T H V (one-block Jacobi), Ritz vectors and residuals
+// of the nroots lowest pairs in one pass over V and W, convergence test, the
+// preconditioned residuals of the unconverged roots as one new block,
+// Gram-Schmidt of that block against V (block classical Gram-Schmidt, second
+// pass by the Daniel-Gragg-Kaufman-Stewart test), then within the block (CGS
+// twice per vector, dropping vectors below 1e-12), H applied to the block and
+// the new columns of G.  In exact arithmetic this is the same basis as
+// vector-by-vector CGS2 of the preconditioned residuals in root order.
 static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, double *h_energies,
                          double *d_C, int *h_iters, double *h_res) {
     cudaStream_t st = ctx->stream;
@@ -593,9 +605,13 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
     if (M < std::min<int64_t>(4 * k, N))
         return sqd_fail(ctx, SQD_EINVAL, "max_subspace must be >= 4*nroots (or the dimension)");
     const int nblk = multidot_blocks(N);
+    const int nbd = block_dot_blocks(ctx, N);
+    const int nbr = 4 * ctx->sm_count;
     const int k2 = std::min(2 * k, M);
     const int kr = std::min(3 * k, M);  // restart basis: 2k Ritz + k previous Ritz
     dav_work w;
+    const int64_t npart = std::max<int64_t>(std::max<int64_t>((int64_t)M * nblk, (int64_t)nbd * M * k),
+                                            (int64_t)nbr * std::max(k, 1));
     SQD_TRY(dalloc(ctx, &w.Vb, (int64_t)M * N));
     SQD_TRY(dalloc(ctx, &w.Wb, (int64_t)M * N));
     SQD_TRY(dalloc(ctx, &w.X, (int64_t)k * N));
@@ -603,46 +619,86 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
     SQD_TRY(dalloc(ctx, &w.Tmp, (int64_t)kr * N));
     SQD_TRY(dalloc(ctx, &w.Yprev, (int64_t)M * k));
     SQD_TRY(dalloc(ctx, &w.Z, (int64_t)M * kr));
+    SQD_TRY(dalloc(ctx, &w.P, (int64_t)M * k));
+    SQD_TRY(dalloc(ctx, &w.GZ, (int64_t)M * kr));
+    SQD_TRY(dalloc(ctx, &w.tn2, k));
     SQD_TRY(dalloc(ctx, &w.rdev, 1));
     SQD_TRY(dalloc(ctx, &w.G, (int64_t)M * M));
     SQD_TRY(dalloc(ctx, &w.evals, M));
     SQD_TRY(dalloc(ctx, &w.evecs, (int64_t)M * M));
     SQD_TRY(dalloc(ctx, &w.dots, M));
-    SQD_TRY(dalloc(ctx, &w.partial, (int64_t)M * nblk));
+    SQD_TRY(dalloc(ctx, &w.partial, npart));
     SQD_TRY(dalloc(ctx, &w.phase, 3 * 4 * ctx->sm_count + 8));
     SQD_TRY(dalloc(ctx, &w.idx, k));
     SQD_TRY(ensure_scratch(ctx, t));
+    const double dN = (double)N;
 
-    auto dot_col = [&](int m, int64_t j) -> int {
-        // G[0..m, j] = Vb[0..m) . Wb_j  (upper triangle column j, m = j+1)
-        return launch_multidot(ctx, w.Vb, N, m, w.Wb + j * N, N, w.partial, nblk,
-                               w.G + j * M);
+    // G[0..m, m0..m0+b) = V[0..m)^T W[m0..m0+b)
+    auto g_cols = [&](int m, int m0, int b) -> int {
+        prof_begin(ctx, PROF_ORTHO);
+        SQD_TRY(launch_block_dot(ctx, w.Vb, N, m, w.Wb + (int64_t)m0 * N, N, b, N, w.partial, nbd,
+                                 w.G + (int64_t)m0 * M, M));
+        prof_end(ctx, 2.0 * m * b * dN, 8.0 * (m + b) * dN);
+        return SQD_OK;
     };
-    // CGS2 of Vb[m] against Vb[0..m); returns its norm^2 on the host
-    auto orthonormalize = [&](int m, double *nrm2) -> int {
-        double *v = w.Vb + (int64_t)m * N;
-        for (int pass = 0; pass < 2; pass++) {
-            if (m == 0) break;
-            SQD_TRY(launch_multidot(ctx, w.Vb, N, m, v, N, w.partial, nblk, w.dots));
-            SQD_TRY(launch_gemv_sub(ctx, w.Vb, N, m, w.dots, v, N));
+    // Orthonormalise the block T = V[m0..m0+b) against V[0..m0) and within
+    // itself; tn2[j] (host) = |T_j|^2 before, or NULL to always take two
+    // passes.  Accepted vectors are packed to V[m0..m0+*nacc).
+    std::vector<double> hP((size_t)M * k), htn2(k);
+    auto orthonormalize_block = [&](int m0, int b, bool have_tn2, int *nacc) -> int {
+        double *T = w.Vb + (int64_t)m0 * N;
+        if (m0 > 0) {
+            for (int pass = 0; pass < 2; pass++) {
+                prof_begin(ctx, PROF_ORTHO);
+                SQD_TRY(launch_block_dot(ctx, w.Vb, N, m0, T, N, b, N, w.partial, nbd, w.P, m0));
+                SQD_TRY(launch_combine_sub(ctx, w.Vb, N, m0, w.P, m0, b, T, N, N));
+                prof_end(ctx, 4.0 * m0 * b * dN, 8.0 * (m0 + 2.0 * b) * dN + 8.0 * m0 * dN);
+                if (pass == 1 || !have_tn2) continue;
+                // DGKS: |T_j|^2 after the pass is |T_j|^2 - |P_j|^2 (V orthonormal);
+                // a second pass unless every vector kept half its squared norm
+                SQD_CUDA(ctx, cudaMemcpyAsync(hP.data(), w.P, sizeof(double) * m0 * b,
+                                              cudaMemcpyDeviceToHost, st));
+                SQD_CUDA(ctx, cudaMemcpyAsync(htn2.data(), w.tn2, sizeof(double) * b,
+                                              cudaMemcpyDeviceToHost, st));
+                SQD_CUDA(ctx, cudaStreamSynchronize(st));
+                bool again = false;
+                for (int j = 0; j < b && !again; j++) {
+                    double p2 = 0.0;
+                    for (int i = 0; i < m0; i++) p2 += hP[i + (size_t)j * m0] * hP[i + (size_t)j * m0];
+                    again = !(p2 <= 0.5 * htn2[j]);
+                }
+                if (!again) break;
+            }
         }
-        SQD_TRY(launch_multidot(ctx, v, N, 1, v, N, w.partial, nblk, w.dots));
-        SQD_CUDA(ctx, cudaMemcpyAsync(nrm2, w.dots, sizeof(double), cudaMemcpyDeviceToHost, st));
-        SQD_CUDA(ctx, cudaStreamSynchronize(st));
+        int acc = 0;
+        for (int j = 0; j < b; j++) {
+            double *dst = T + (int64_t)acc * N;
+            if (acc != j)
+                SQD_CUDA(ctx, cudaMemcpyAsync(dst, T + (int64_t)j * N, sizeof(double) * N,
+                                              cudaMemcpyDeviceToDevice, st));
+            prof_begin(ctx, PROF_ORTHO);
+            for (int pass = 0; pass < 2 && acc > 0; pass++) {
+                SQD_TRY(launch_multidot(ctx, T, N, acc, dst, N, w.partial, nblk, w.dots));
+                SQD_TRY(launch_gemv_sub(ctx, T, N, acc, w.dots, dst, N));
+            }
+            SQD_TRY(launch_multidot(ctx, dst, N, 1, dst, N, w.partial, nblk, w.dots));
+            prof_end(ctx, (8.0 * acc + 2.0) * dN, 8.0 * (4.0 * acc + 5.0) * dN);
+            double n2 = 0.0;
+            SQD_CUDA(ctx, cudaMemcpyAsync(&n2, w.dots, sizeof(double), cudaMemcpyDeviceToHost, st));
+            SQD_CUDA(ctx, cudaStreamSynchronize(st));
+            if (!(std::sqrt(n2) >= 1e-12)) continue;  // dropped
+            SQD_TRY(launch_scale(ctx, dst, N, w.dots, 1));
+            acc++;
+        }
+        *nacc = acc;
         return SQD_OK;
     };
 
     int m = 0;
     if (o->use_guess) {
-        for (int j = 0; j < k; j++) {
-            SQD_CUDA(ctx, cudaMemcpyAsync(w.Vb + (int64_t)m * N, d_C + (int64_t)j * N,
-                                          sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-            double n2 = 0.0;
-            SQD_TRY(orthonormalize(m, &n2));
-            if (!(std::sqrt(n2) >= 1e-12)) continue;
-            SQD_TRY(launch_scale(ctx, w.Vb + (int64_t)m * N, N, w.dots, 1));
-            m++;
-        }
+        SQD_CUDA(ctx, cudaMemcpyAsync(w.Vb, d_C, sizeof(double) * k * N, cudaMemcpyDeviceToDevice,
+                                      st));
+        SQD_TRY(orthonormalize_block(0, k, false, &m));
         if (m < k) return sqd_fail(ctx, SQD_EINVAL, "initial guess vectors are linearly dependent");
     } else {
         SQD_CUDA(ctx, cudaMemsetAsync(w.Vb, 0, sizeof(double) * k * N, st));
@@ -657,20 +713,20 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
     if (o->use_stored_h && !t->st_rowptr)
         return sqd_fail(ctx, SQD_EINVAL, "use_stored_h set but sqd_stored_h_build was not called");
     SQD_TRY(apply_h(w.Vb, w.Wb, m));
-    for (int j = 0; j < m; j++) SQD_TRY(dot_col(j + 1, j));
+    SQD_TRY(g_cols(m, 0, m));
 
     std::vector<double> theta(M), theta_old(k, INFINITY), rn2(k), rn(k);
     int it = 0;
     int mprev = 0;  // rows of Yprev (0: no previous Ritz vectors yet)
     int status = SQD_OK;
     for (;;) {
+        prof_begin(ctx, PROF_EIGH);
         SQD_TRY(launch_jacobi_eigh(ctx, w.G, M, m, w.evals, w.evecs));
-        SQD_TRY(launch_combine(ctx, w.Vb, N, m, w.evecs, m, k, w.X, N, N));
-        SQD_TRY(launch_combine(ctx, w.Wb, N, m, w.evecs, m, k, w.R, N, N));
-        SQD_TRY(launch_residual(ctx, w.X, w.R, w.evals, k, N, w.R));
-        for (int j = 0; j < k; j++)
-            SQD_TRY(launch_multidot(ctx, w.R + (int64_t)j * N, N, 1, w.R + (int64_t)j * N, N,
-                                    w.partial, nblk, w.dots + j));
+        prof_end(ctx, 0.0, 0.0);
+        prof_begin(ctx, PROF_DAVIDSON);
+        SQD_TRY(launch_ritz_block(ctx, w.Vb, w.Wb, N, m, w.evecs, w.evals, k, w.X, w.R, N,
+                                  w.partial, nbr, w.dots));
+        prof_end(ctx, 4.0 * m * k * dN + 2.0 * k * dN, 8.0 * (2.0 * m + 2.0 * k) * dN);
         SQD_CUDA(ctx, cudaMemcpyAsync(theta.data(), w.evals, sizeof(double) * m,
                                       cudaMemcpyDeviceToHost, st));
         SQD_CUDA(ctx, cudaMemcpyAsync(rn2.data(), w.dots, sizeof(double) * k,
@@ -702,14 +758,17 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
             int r = m2;
             SQD_CUDA(ctx, cudaMemcpyAsync(&r, w.rdev, sizeof(int), cudaMemcpyDeviceToHost, st));
             SQD_CUDA(ctx, cudaStreamSynchronize(st));
+            prof_begin(ctx, PROF_DAVIDSON);
             SQD_TRY(launch_combine(ctx, w.Vb, N, m, w.Z, M, r, w.Tmp, N, N));
             SQD_CUDA(ctx, cudaMemcpyAsync(w.Vb, w.Tmp, sizeof(double) * r * N,
                                           cudaMemcpyDeviceToDevice, st));
             SQD_TRY(launch_combine(ctx, w.Wb, N, m, w.Z, M, r, w.Tmp, N, N));
             SQD_CUDA(ctx, cudaMemcpyAsync(w.Wb, w.Tmp, sizeof(double) * r * N,
                                           cudaMemcpyDeviceToDevice, st));
+            // projected matrix of the new basis: G' = Z^T G Z
+            SQD_TRY(launch_project_g(ctx, w.G, M, m, w.Z, M, r, w.GZ));
+            prof_end(ctx, 4.0 * m * r * dN, 8.0 * (2.0 * m + 4.0 * r) * dN);
             m = r;
-            for (int j = 0; j < m; j++) SQD_TRY(dot_col(j + 1, j));
             // the current Ritz vectors are the first k basis vectors now
             SQD_TRY(launch_identity_cols(ctx, w.Yprev, m, k, M));
             mprev = m;
@@ -719,25 +778,26 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
                                             cudaMemcpyDeviceToDevice, st));
             mprev = m;
         }
-        int m_old = m;
-        for (int j : todo) {
-            double *v = w.Vb + (int64_t)m * N;
-            SQD_TRY(launch_precondition(ctx, w.R + (int64_t)j * N, t->diag, theta[j],
-                                        o->precond_floor, N, v));
-            double n2 = 0.0;
-            SQD_TRY(orthonormalize(m, &n2));
-            if (!(std::sqrt(n2) >= 1e-12)) continue;  // dropped
-            SQD_TRY(launch_scale(ctx, v, N, w.dots, 1));
-            m++;
+        const int m_old = m, b = (int)todo.size();
+        prof_begin(ctx, PROF_DAVIDSON);
+        for (int q = 0; q < b; q++) {
+            const int j = todo[q];
+            SQD_TRY(launch_precondition_norm(ctx, w.R + (int64_t)j * N, t->diag, theta[j],
+                                             o->precond_floor, N, w.Vb + (int64_t)(m_old + q) * N,
+                                             w.partial, w.tn2 + q));
         }
-        if (m == m_old) {
+        prof_end(ctx, 2.0 * b * dN, 24.0 * b * dN);
+        int nacc = 0;
+        SQD_TRY(orthonormalize_block(m_old, b, true, &nacc));
+        m = m_old + nacc;
+        if (nacc == 0) {
             bool res_ok = true;
             for (int j = 0; j < k; j++) res_ok = res_ok && rn[j] <= o->tol_residual;
             if (!res_ok) status = SQD_EBREAKDOWN;
             break;
         }
-        SQD_TRY(apply_h(w.Vb + (int64_t)m_old * N, w.Wb + (int64_t)m_old * N, m - m_old));
-        for (int j = m_old; j < m; j++) SQD_TRY(dot_col(j + 1, j));
+        SQD_TRY(apply_h(w.Vb + (int64_t)m_old * N, w.Wb + (int64_t)m_old * N, nacc));
+        SQD_TRY(g_cols(m, m_old, nacc));
     }
     // outputs: Ritz vectors with the phase fixed, energies, residuals
     SQD_CUDA(ctx, cudaMemcpyAsync(d_C, w.X, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, st));

@@ -24,9 +24,20 @@ __global__ void __launch_bounds__(RED_THREADS)
     int64_t lo = per * blockIdx.x, hi = min(n, lo + per);
     for (int i = 0; i < m; i++) {
         const double *a = A + (int64_t)i * lda;
-        double s = 0.0;
-        for (int64_t j = lo + threadIdx.x; j < hi; j += RED_THREADS) s = fma(a[j], x[j], s);
-        double t = block_sum(s, sh);
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int64_t j = lo + threadIdx.x;
+        for (; j + 3 * RED_THREADS < hi; j += 4 * RED_THREADS) {
+            const double a0 = a[j], a1 = a[j + RED_THREADS], a2 = a[j + 2 * RED_THREADS],
+                         a3 = a[j + 3 * RED_THREADS];
+            const double x0 = x[j], x1 = x[j + RED_THREADS], x2 = x[j + 2 * RED_THREADS],
+                         x3 = x[j + 3 * RED_THREADS];
+            s0 = fma(a0, x0, s0);
+            s1 = fma(a1, x1, s1);
+            s2 = fma(a2, x2, s2);
+            s3 = fma(a3, x3, s3);
+        }
+        for (; j < hi; j += RED_THREADS) s0 = fma(a[j], x[j], s0);
+        double t = block_sum((s0 + s1) + (s2 + s3), sh);
         if (threadIdx.x == 0) partial[(int64_t)i * gridDim.x + blockIdx.x] = t;
     }
 }
@@ -50,51 +61,48 @@ int launch_multidot(sqd_ctx *ctx, const double *A, int64_t lda, int m, const dou
     return SQD_OK;
 }
 
-// x[n] -= sum_i A_i[n] c[i]
-__global__ void k_gemv_sub(const double *__restrict__ A, int64_t lda, int m,
-                           const double *__restrict__ c, double *__restrict__ x, int64_t n) {
-    __shared__ double cs[256];
-    for (int i = threadIdx.x; i < m; i += blockDim.x) cs[i] = c[i];
-    __syncthreads();
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int i = 0; i < m; i++) s = fma(A[(int64_t)i * lda + j], cs[i], s);
-        x[j] -= s;
-    }
-}
-
-int launch_gemv_sub(sqd_ctx *ctx, const double *A, int64_t lda, int m, const double *c,
-                    double *x, int64_t n) {
-    if (m == 0 || n == 0) return SQD_OK;
-    if (m > 256) return sqd_fail(ctx, SQD_EINVAL, "basis too large");
-    unsigned g = grid_1d(n, 256);
-    if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
-    k_gemv_sub<<<g, 256, 0, ctx->stream>>>(A, lda, m, c, x, n);
-    SQD_LAUNCHED(ctx);
-    return SQD_OK;
-}
-
-// out_j[n] = sum_i A_i[n] Y[i + j*ldy], j < k
-__global__ void k_combine(const double *__restrict__ A, int64_t lda, int m,
-                          const double *__restrict__ Y, int ldy, int k, double *__restrict__ out,
-                          int64_t ldo, int64_t n) {
+// out_j[n] = sum_i A_i[n] Y[i + j*ldy], j < k  (sub: out_j[n] -= that sum).
+// Each thread keeps 8 loads of A in flight (the basis does not fit in L2, so
+// the loop is bound by HBM latency otherwise) and up to 8 outputs in
+// registers; A is read once per group of 8 outputs.
+#define CB_U 8
+__global__ void __launch_bounds__(256) k_combine(const double *__restrict__ A, int64_t lda, int m,
+                                                 const double *__restrict__ Y, int ldy, int k,
+                                                 double *__restrict__ out, int64_t ldo, int64_t n,
+                                                 int sub) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         for (int j0 = 0; j0 < k; j0 += 8) {
             double acc[8];
 #pragma unroll
             for (int q = 0; q < 8; q++) acc[q] = 0.0;
-            int jn = min(8, k - j0);
-            for (int i = 0; i < m; i++) {
-                double a = A[(int64_t)i * lda + p];
+            const int jn = min(8, k - j0);
+            const double *Yj = Y + (int64_t)j0 * ldy;
+            int i = 0;
+            for (; i + CB_U <= m; i += CB_U) {
+                double a[CB_U];
+#pragma unroll
+                for (int u = 0; u < CB_U; u++) a[u] = A[(int64_t)(i + u) * lda + p];
+#pragma unroll
+                for (int u = 0; u < CB_U; u++) {
+#pragma unroll
+                    for (int q = 0; q < 8; q++)
+                        if (q < jn) acc[q] = fma(a[u], __ldg(Yj + i + u + (int64_t)q * ldy), acc[q]);
+                }
+            }
+            for (; i < m; i++) {
+                const double a = A[(int64_t)i * lda + p];
 #pragma unroll
                 for (int q = 0; q < 8; q++)
-                    if (q < jn) acc[q] = fma(a, __ldg(Y + i + (int64_t)(j0 + q) * ldy), acc[q]);
+                    if (q < jn) acc[q] = fma(a, __ldg(Yj + i + (int64_t)q * ldy), acc[q]);
             }
 #pragma unroll
-            for (int q = 0; q < 8; q++)
-                if (q < jn) out[(int64_t)(j0 + q) * ldo + p] = acc[q];
+            for (int q = 0; q < 8; q++) {
+                if (q < jn) {
+                    double *o = out + (int64_t)(j0 + q) * ldo + p;
+                    *o = sub ? *o - acc[q] : acc[q];
+                }
+            }
         }
     }
 }
@@ -104,7 +112,278 @@ int launch_combine(sqd_ctx *ctx, const double *A, int64_t lda, int m, const doub
     if (k == 0 || n == 0) return SQD_OK;
     unsigned g = grid_1d(n, 256);
     if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
-    k_combine<<<g, 256, 0, ctx->stream>>>(A, lda, m, Y, ldy, k, out, ldo, n);
+    k_combine<<<g, 256, 0, ctx->stream>>>(A, lda, m, Y, ldy, k, out, ldo, n, 0);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// x[n] -= sum_i A_i[n] c[i]: one Gram-Schmidt update
+int launch_gemv_sub(sqd_ctx *ctx, const double *A, int64_t lda, int m, const double *c,
+                    double *x, int64_t n) {
+    if (m == 0 || n == 0) return SQD_OK;
+    unsigned g = grid_1d(n, 256);
+    if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
+    k_combine<<<g, 256, 0, ctx->stream>>>(A, lda, m, c, m, 1, x, n, n, 1);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// out_j[n] -= sum_i A_i[n] Y[i + j*ldy], j < k: the update of block Gram-Schmidt
+int launch_combine_sub(sqd_ctx *ctx, const double *A, int64_t lda, int m, const double *Y,
+                       int ldy, int k, double *out, int64_t ldo, int64_t n) {
+    if (k == 0 || m == 0 || n == 0) return SQD_OK;
+    unsigned g = grid_1d(n, 256);
+    if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
+    k_combine<<<g, 256, 0, ctx->stream>>>(A, lda, m, Y, ldy, k, out, ldo, n, 1);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// ------------------------------------------------- block dot products ---
+// out[i + j*ldo] = sum_n A_i[n] X_j[n] for i < m, j < b: a tall-skinny
+// product split over n.  Each block walks its n-range in tiles of kc columns
+// staged in shared memory (every element of A and X is read from HBM once),
+// kc chosen so that the m + b rows of a tile fill about BD_TILE doubles.  The
+// m*b outputs are spread over the 256 threads; when there are fewer outputs
+// than threads, g = 256 / (m*b) threads share an output and split the tile's
+// columns, and their sums are added at the end.  The per-block partials are
+// summed in a fixed order, so results do not depend on timing.
+#define BD_TILE 4608
+#define BD_MAXB 32
+#define BD_OUT 16
+
+int block_dot_blocks(const sqd_ctx *ctx, int64_t n) {
+    int64_t b = (n + 4095) / 4096;
+    const int64_t cap = 4LL * ctx->sm_count;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+static int block_dot_kc(int m, int b) {
+    int kc = (BD_TILE / (m + b) - 1) / 32 * 32;
+    return kc < 32 ? 32 : (kc > 512 ? 512 : kc);
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+    k_block_dot_partial(const double *__restrict__ A, int64_t lda, int m,
+                        const double *__restrict__ X, int64_t ldx, int b, int64_t n, int kc,
+                        double *__restrict__ partial) {
+    extern __shared__ double bd_sh[];
+    const int ld = kc + 1;
+    double *As = bd_sh, *Xs = bd_sh + (size_t)m * ld;
+    const int mb = m * b;
+    const int g = (mb >= RED_THREADS) ? 1 : RED_THREADS / mb;  // threads per output
+    const int tg = threadIdx.x / mb;                             // column group (g > 1)
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = per * blockIdx.x, hi = min(n, lo + per);
+    double acc[BD_OUT];
+#pragma unroll
+    for (int q = 0; q < BD_OUT; q++) acc[q] = 0.0;
+    for (int64_t c0 = lo; c0 < hi; c0 += kc) {
+        const int len = (int)min((int64_t)kc, hi - c0);
+        const int rows = m + b;
+#pragma unroll 8
+        for (int t = threadIdx.x; t < rows * kc; t += RED_THREADS) {
+            const int r = t / kc, kk = t - r * kc;
+            const double *src = (r < m) ? A + (int64_t)r * lda : X + (int64_t)(r - m) * ldx;
+            bd_sh[(size_t)r * ld + kk] = (kk < len) ? src[c0 + kk] : 0.0;
+        }
+        __syncthreads();
+        if (g == 1) {
+#pragma unroll
+            for (int q = 0; q < BD_OUT; q++) {
+                const int o = threadIdx.x + q * RED_THREADS;
+                if (o < mb) {
+                    const double *ar = As + (size_t)(o % m) * ld, *xr = Xs + (size_t)(o / m) * ld;
+                    double s = acc[q];
+#pragma unroll 8
+                    for (int kk = 0; kk < kc; kk++) s = fma(ar[kk], xr[kk], s);
+                    acc[q] = s;
+                }
+            }
+        } else if (tg < g) {
+            const int o = threadIdx.x - tg * mb;
+            const double *ar = As + (size_t)(o % m) * ld, *xr = Xs + (size_t)(o / m) * ld;
+            double s = acc[0];
+#pragma unroll 4
+            for (int kk = tg; kk < kc; kk += g) s = fma(ar[kk], xr[kk], s);
+            acc[0] = s;
+        }
+        __syncthreads();
+    }
+    if (g == 1) {
+#pragma unroll
+        for (int q = 0; q < BD_OUT; q++) {
+            const int o = threadIdx.x + q * RED_THREADS;
+            if (o < mb) partial[(int64_t)blockIdx.x * mb + o] = acc[q];
+        }
+    } else {
+        // fixed-order sum over the g column groups of each output
+        bd_sh[threadIdx.x] = (tg < g) ? acc[0] : 0.0;
+        __syncthreads();
+        if (threadIdx.x < mb) {
+            double s = 0.0;
+            for (int q = 0; q < g; q++) s += bd_sh[threadIdx.x + q * mb];
+            partial[(int64_t)blockIdx.x * mb + threadIdx.x] = s;
+        }
+    }
+}
+
+__global__ void k_block_dot_final(const double *__restrict__ partial, int nblk, int m, int b,
+                                  double *__restrict__ out, int ldo) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    const int mb = m * b;
+    if (o >= mb) return;
+    double s = 0.0;
+    for (int blk = 0; blk < nblk; blk++) s += partial[(int64_t)blk * mb + o];
+    out[(o % m) + (int64_t)(o / m) * ldo] = s;
+}
+
+int launch_block_dot(sqd_ctx *ctx, const double *A, int64_t lda, int m, const double *X,
+                     int64_t ldx, int b, int64_t n, double *partial, int nblk, double *out,
+                     int ldo) {
+    if (m == 0 || b == 0) return SQD_OK;
+    if (m > JAC_MAX || b > BD_MAXB || m * b > RED_THREADS * BD_OUT)
+        return sqd_fail(ctx, SQD_EINVAL, "block dot of %d x %d vectors out of range", m, b);
+    const int kc = block_dot_kc(m, b);
+    size_t shm = sizeof(double) * (size_t)(m + b) * (kc + 1);
+    if (shm < sizeof(double) * RED_THREADS) shm = sizeof(double) * RED_THREADS;
+    // at most (112 + 32) rows x 33 columns = 38 KB: within the default 48 KB
+    k_block_dot_partial<<<nblk, RED_THREADS, shm, ctx->stream>>>(A, lda, m, X, ldx, b, n, kc,
+                                                                  partial);
+    SQD_LAUNCHED(ctx);
+    k_block_dot_final<<<(m * b + 127) / 128, 128, 0, ctx->stream>>>(partial, nblk, m, b, out, ldo);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// ------------------------------------------------- Ritz vectors, residuals --
+// For the k lowest Ritz pairs (theta_j, y_j): X_j = V y_j, R_j = W y_j -
+// theta_j X_j, and per-block partial sums of |R_j|^2 (partial[blk*k + j]).
+// V and W are read once per group of 8 roots.
+__global__ void __launch_bounds__(RED_THREADS)
+    k_ritz_block(const double *__restrict__ V, const double *__restrict__ W, int64_t ld, int m,
+                 const double *__restrict__ Y, const double *__restrict__ theta, int k,
+                 double *__restrict__ X, double *__restrict__ R, int64_t n,
+                 double *__restrict__ partial) {
+    __shared__ double red[32];
+    for (int j0 = 0; j0 < k; j0 += 8) {
+        const int jn = min(8, k - j0);
+        double ss[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) ss[q] = 0.0;
+        for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+             p += (int64_t)gridDim.x * blockDim.x) {
+            double xa[8], wa[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) xa[q] = wa[q] = 0.0;
+            int i = 0;
+            for (; i + 4 <= m; i += 4) {
+                double v[4], w[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    v[u] = V[(int64_t)(i + u) * ld + p];
+                    w[u] = W[(int64_t)(i + u) * ld + p];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        if (q < jn) {
+                            const double y = __ldg(Y + i + u + (int64_t)(j0 + q) * m);
+                            xa[q] = fma(v[u], y, xa[q]);
+                            wa[q] = fma(w[u], y, wa[q]);
+                        }
+                    }
+                }
+            }
+            for (; i < m; i++) {
+                const double v = V[(int64_t)i * ld + p], w = W[(int64_t)i * ld + p];
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    if (q < jn) {
+                        const double y = __ldg(Y + i + (int64_t)(j0 + q) * m);
+                        xa[q] = fma(v, y, xa[q]);
+                        wa[q] = fma(w, y, wa[q]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                if (q < jn) {
+                    const double r = fma(-__ldg(theta + j0 + q), xa[q], wa[q]);
+                    X[(int64_t)(j0 + q) * ld + p] = xa[q];
+                    R[(int64_t)(j0 + q) * ld + p] = r;
+                    ss[q] = fma(r, r, ss[q]);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            if (q < jn) {  // uniform across the block
+                const double t = block_sum(ss[q], red);
+                if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * k + j0 + q] = t;
+            }
+        }
+    }
+}
+
+__global__ void k_ritz_final(const double *__restrict__ partial, int nblk, int k,
+                             double *__restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= k) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; b++) s += partial[(int64_t)b * k + j];
+    out[j] = s;
+}
+
+int launch_ritz_block(sqd_ctx *ctx, const double *V, const double *W, int64_t ld, int m,
+                      const double *Y, const double *theta, int k, double *X, double *R,
+                      int64_t n, double *partial, int nblk, double *rnorm2) {
+    if (k == 0 || n == 0) return SQD_OK;
+    k_ritz_block<<<nblk, RED_THREADS, 0, ctx->stream>>>(V, W, ld, m, Y, theta, k, X, R, n,
+                                                        partial);
+    SQD_LAUNCHED(ctx);
+    k_ritz_final<<<(k + 63) / 64, 64, 0, ctx->stream>>>(partial, nblk, k, rnorm2);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// ------------------------------------------- projected matrix at restart --
+// After V' = V Z, W' = W Z the projected matrix is G' = Z^T G Z (G symmetric,
+// upper triangle stored with leading dimension ldg).  GZ (m x r, ld m) is a
+// scratch buffer; the upper triangle of G'[0..r) overwrites G.
+__global__ void k_gz(const double *__restrict__ G, int ldg, int m, const double *__restrict__ Z,
+                     int ldz, int r, double *__restrict__ GZ) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m * r) return;
+    const int i = t % m, j = t / m;
+    double s = 0.0;
+    for (int q = 0; q < m; q++) {
+        const double g = (i <= q) ? G[i + (int64_t)q * ldg] : G[q + (int64_t)i * ldg];
+        s = fma(g, Z[q + (int64_t)j * ldz], s);
+    }
+    GZ[i + (int64_t)j * m] = s;
+}
+
+__global__ void k_ztgz(double *__restrict__ G, int ldg, int m, const double *__restrict__ Z,
+                       int ldz, int r, const double *__restrict__ GZ) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= r * r) return;
+    const int i = t % r, j = t / r;
+    if (i > j) return;
+    double s = 0.0;
+    for (int q = 0; q < m; q++) s = fma(Z[q + (int64_t)i * ldz], GZ[q + (int64_t)j * m], s);
+    G[i + (int64_t)j * ldg] = s;
+}
+
+int launch_project_g(sqd_ctx *ctx, double *G, int ldg, int m, const double *Z, int ldz, int r,
+                     double *GZ) {
+    if (m == 0 || r == 0) return SQD_OK;
+    k_gz<<<(m * r + 127) / 128, 128, 0, ctx->stream>>>(G, ldg, m, Z, ldz, r, GZ);
+    SQD_LAUNCHED(ctx);
+    k_ztgz<<<(r * r + 127) / 128, 128, 0, ctx->stream>>>(G, ldg, m, Z, ldz, r, GZ);
     SQD_LAUNCHED(ctx);
     return SQD_OK;
 }
@@ -130,23 +409,51 @@ int launch_residual(sqd_ctx *ctx, const double *X, const double *WY, const doubl
     return SQD_OK;
 }
 
-// T = R / (theta - diag), |denominator| clamped to floor_ (sign kept, + for 0)
-__global__ void k_precondition(const double *__restrict__ R, const double *__restrict__ diag,
-                               double theta, double floor_, int64_t n, double *__restrict__ T) {
+// T = R / (theta - diag), |denominator| clamped to floor_ (sign kept, + for 0);
+// with partial != NULL also per-block partial sums of T^2
+__global__ void __launch_bounds__(RED_THREADS)
+    k_precondition(const double *__restrict__ R, const double *__restrict__ diag, double theta,
+                   double floor_, int64_t n, double *__restrict__ T, double *__restrict__ partial) {
+    __shared__ double red[32];
+    double ss = 0.0;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         double d = theta - diag[p];
         if (fabs(d) < floor_) d = (d < 0.0) ? -floor_ : floor_;
-        T[p] = R[p] / d;
+        const double t = R[p] / d;
+        T[p] = t;
+        ss = fma(t, t, ss);
     }
+    if (partial) {
+        const double tot = block_sum(ss, red);
+        if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+    }
+}
+
+static unsigned precondition_grid(const sqd_ctx *ctx, int64_t n) {
+    unsigned g = grid_1d(n, RED_THREADS);
+    if (g > 4u * (unsigned)ctx->sm_count) g = 4u * (unsigned)ctx->sm_count;
+    return g;
 }
 
 int launch_precondition(sqd_ctx *ctx, const double *R, const double *diag, double theta,
                         double floor_, int64_t n, double *T) {
     if (n == 0) return SQD_OK;
-    unsigned g = grid_1d(n, 256);
-    if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
-    k_precondition<<<g, 256, 0, ctx->stream>>>(R, diag, theta, floor_, n, T);
+    k_precondition<<<precondition_grid(ctx, n), RED_THREADS, 0, ctx->stream>>>(
+        R, diag, theta, floor_, n, T, nullptr);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// the same, and *norm2 (device) = |T|^2; partial holds 4 * SMs doubles
+int launch_precondition_norm(sqd_ctx *ctx, const double *R, const double *diag, double theta,
+                             double floor_, int64_t n, double *T, double *partial,
+                             double *norm2) {
+    if (n == 0) return SQD_OK;
+    const unsigned g = precondition_grid(ctx, n);
+    k_precondition<<<g, RED_THREADS, 0, ctx->stream>>>(R, diag, theta, floor_, n, T, partial);
+    SQD_LAUNCHED(ctx);
+    k_multidot_final<<<1, 64, 0, ctx->stream>>>(partial, (int)g, 1, norm2);
     SQD_LAUNCHED(ctx);
     return SQD_OK;
 }

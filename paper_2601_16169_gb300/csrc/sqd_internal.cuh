@@ -17,9 +17,11 @@ enum prof_class {
     PROF_TRANSPOSE,       // C -> C^T and the transposed add-back
     PROF_TABLES,          // excitation tables, string terms, diagonal
     PROF_STRINGS,         // string filtering, sort, scan
-    PROF_DAVIDSON,        // Davidson vector kernels and the Jacobi solver
+    PROF_DAVIDSON,        // Davidson Ritz vectors, residuals, preconditioner, restart
     PROF_RDM,             // density matrices
     PROF_STORED,          // stored-H sparse matrix-vector product
+    PROF_ORTHO,           // Davidson Gram-Schmidt and projected-matrix columns
+    PROF_EIGH,            // Davidson Rayleigh-Ritz eigensolver
     PROF_NCLASS
 };
 
@@ -205,10 +207,24 @@ int launch_gemv_sub(sqd_ctx *, const double *A, int64_t lda, int m, const double
                     double *x, int64_t n);
 int launch_combine(sqd_ctx *, const double *A, int64_t lda, int m, const double *Y,
                    int ldy, int k, double *out, int64_t ldo, int64_t n);
+int launch_combine_sub(sqd_ctx *, const double *A, int64_t lda, int m, const double *Y,
+                       int ldy, int k, double *out, int64_t ldo, int64_t n);
+int block_dot_blocks(const sqd_ctx *, int64_t n);
+int launch_block_dot(sqd_ctx *, const double *A, int64_t lda, int m, const double *X,
+                     int64_t ldx, int b, int64_t n, double *partial, int nblk, double *out,
+                     int ldo);
+int launch_ritz_block(sqd_ctx *, const double *V, const double *W, int64_t ld, int m,
+                      const double *Y, const double *theta, int k, double *X, double *R,
+                      int64_t n, double *partial, int nblk, double *rnorm2);
+int launch_project_g(sqd_ctx *, double *G, int ldg, int m, const double *Z, int ldz, int r,
+                     double *GZ);
 int launch_residual(sqd_ctx *, const double *X, const double *WY, const double *theta,
                     int k, int64_t n, double *R);
 int launch_precondition(sqd_ctx *, const double *R, const double *diag, double theta,
                         double floor_, int64_t n, double *T);
+int launch_precondition_norm(sqd_ctx *, const double *R, const double *diag, double theta,
+                             double floor_, int64_t n, double *T, double *partial,
+                             double *norm2);
 int launch_scale(sqd_ctx *, double *x, int64_t n, const double *s_dev, int invert_sqrt);
 int launch_jacobi_eigh(sqd_ctx *, const double *G, int ldg, int m, double *evals,
                        double *evecs);

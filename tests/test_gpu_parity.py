@@ -122,6 +122,25 @@ def test_tables_bit_exact(sqd, ctx, name):
     t.close()
 
 
+def test_tables_match_golden_digest(sqd, ctx):
+    # the full-size h2o29 lists against the stored oracle digest
+    from tests.golden import make_golden as mg
+    ref = mg.read_tables()
+    w = si.workload("h2o29")
+    t = make_tables(sqd, ctx, w.norb, w.strings_a, 5, w.strings_b, 5, w.h, w.V)
+    for kind, name in ((1, "singles"), (2, "doubles")):
+        g = t.export(0, kind)
+        orb = np.asarray(g["orb"], dtype=np.int64).reshape(len(g["tgt"]), -1)
+        got = {"nnz": int(g["off"][-1]), "max_per_string": int(np.diff(g["off"]).max()),
+               "sum_target": int(np.sum(g["tgt"], dtype=np.int64)),
+               "sum_sign": int(np.sum(g["sign"], dtype=np.int64)),
+               "sum_orbital_code": int(np.sum(orb * np.arange(1, orb.shape[1] + 1),
+                                              dtype=np.int64))}
+        for key, val in got.items():
+            assert ref["%s.%s" % (name, key)] == val, (name, key)
+    t.close()
+
+
 def test_tables_info_counts(sqd, ctx):
     norb, sa, na_e, sb, nb_e, h, V, ecore = case("uneven")
     t = make_tables(sqd, ctx, norb, sa, na_e, sb, nb_e, h, V, ecore)
@@ -224,6 +243,50 @@ def test_davidson_multiroot_vs_lapack(sqd, ctx, name):
     Xh = X.cpu().numpy().reshape(4, -1)
     assert np.allclose(Xh @ Xh.T, np.eye(4), atol=1e-10)
     assert np.all(np.linalg.norm(Xh @ H - e[:, None] * Xh, axis=1) <= 1e-7)
+    t.close()
+
+
+def test_davidson_full8_golden(sqd, ctx):
+    from tests.golden import make_golden as mg
+    w = si.workload("full8")
+    t = make_tables(sqd, ctx, w.norb, w.strings_a, 4, w.strings_b, 4, w.h, w.V)
+    e, X, it, res, rc = sqd.davidson(ctx, t, nroots=4, tol_residual=1e-8, tol_energy=1e-12)
+    assert np.max(np.abs(e - mg.read_full8())) <= 1e-10
+    t.close()
+
+
+def test_davidson_exhausts_tiny_space(sqd, ctx):
+    # 36 determinants, 6 roots, a subspace as large as the space: the new
+    # blocks become linearly dependent on the basis and vectors are dropped
+    # inside a block; the energies must still be the exact lowest six
+    norb = 4
+    s = si.full_strings(norb, 2)
+    h, V = si.make_integrals(norb, 8, 77)
+    t = make_tables(sqd, ctx, norb, s, 2, s, 2, h, V)
+    H = oracle.dense_h(norb, h, V, 0.0, s, s)
+    ref = np.linalg.eigvalsh(H)[:6]
+    e, X, it, res, rc = sqd.davidson(ctx, t, nroots=6, tol_residual=1e-9, tol_energy=1e-12,
+                                     max_subspace=36)
+    assert np.max(np.abs(e - ref)) <= 1e-10
+    Xh = X.cpu().numpy().reshape(6, -1)
+    assert np.allclose(Xh @ Xh.T, np.eye(6), atol=1e-10)
+    t.close()
+
+
+def test_davidson_guess_block_dependent(sqd, ctx):
+    # a guess block with two equal vectors is rejected; an exact eigenvector
+    # guess converges at once to the same energy
+    w = si.workload("full8")
+    t = make_tables(sqd, ctx, w.norb, w.strings_a, 4, w.strings_b, 4, w.h, w.V)
+    H = oracle.dense_h(w.norb, w.h, w.V, 0.0, w.strings_a, w.strings_b)
+    ev, U = np.linalg.eigh(H)
+    g = np.stack([U[:, 0], U[:, 0]]).reshape(2, 70, 70)
+    with pytest.raises(sqd.SQDError):
+        sqd.davidson(ctx, t, nroots=2, guess=dev_f64(g))
+    g = np.stack([U[:, 0], U[:, 1]]).reshape(2, 70, 70)
+    e, X, it, res, rc = sqd.davidson(ctx, t, nroots=2, guess=dev_f64(g), tol_residual=1e-8,
+                                     tol_energy=1e-10)
+    assert np.max(np.abs(e - ev[:2])) <= 1e-10 and it <= 2
     t.close()
 
 
