@@ -154,7 +154,9 @@ void sqd_free_tables(sqd_tables *tables);
  *  [0] norb, [1] n_alpha, [2] n_beta, [3] nnz singles alpha, [4] nnz doubles
  *  alpha, [5] nnz singles beta, [6] nnz doubles beta, [7] shared (1 if one
  *  table serves both spins), [8] device bytes held, [9] max singles per
- *  string, [10] max doubles per string, [11] reserved. */
+ *  string, [10] max doubles per string, [11] alpha row groups of the
+ *  paired-singles work split (chosen by timing candidates on the first
+ *  sigma of each sigma mode). */
 int sqd_tables_info(const sqd_tables *tables, int64_t *info);
 
 /*

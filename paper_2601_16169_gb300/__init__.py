@@ -216,7 +216,8 @@ class Tables:
         buf = (ctypes.c_int64 * 12)()
         self.ctx._check(self.ctx._lib.sqd_tables_info(self.handle, buf))
         keys = ["norb", "n_alpha", "n_beta", "nnz1_alpha", "nnz2_alpha", "nnz1_beta",
-                "nnz2_beta", "shared", "device_bytes", "max_singles", "max_doubles"]
+                "nnz2_beta", "shared", "device_bytes", "max_singles", "max_doubles",
+                "ab_groups"]
         return {k: int(buf[i]) for i, k in enumerate(keys)}
 
     def set_sigma_mode(self, mode: int):

@@ -444,7 +444,7 @@ int sqd_tables_info(const sqd_tables *t, int64_t *info) {
     info[8] = t->bytes;
     info[9] = std::max(t->a.max1, t->b->max1);
     info[10] = std::max(t->a.max2, t->b->max2);
-    info[11] = 0;
+    info[11] = t->ab.ngroups;
     return SQD_OK;
 }
 
@@ -522,6 +522,10 @@ static void sigma_work(const sqd_tables *t, double *f_a, double *f_b, double *f_
     *f_ab = 2.0 * (double)t->a.nnz1 * (double)t->b->nnz1;
 }
 
+static int ab_launch_fp64(sqd_ctx *ctx, sqd_tables *t, const void *C, double *S) {
+    return launch_alpha_beta(ctx, t, (const double *)C, S);
+}
+
 static int sigma_impl(sqd_ctx *ctx, sqd_tables *t, const double *C, double *S, int nvec) {
     const int64_t na = t->a.n, nb = t->b->n, N = na * nb;
     const double vb = 8.0 * (double)N;
@@ -534,6 +538,7 @@ static int sigma_impl(sqd_ctx *ctx, sqd_tables *t, const double *C, double *S, i
             SQD_TRY(sigma_df_one(ctx, t, C + (int64_t)v * N, S + (int64_t)v * N, f_a, f_b, f_ab));
         return SQD_OK;
     }
+    SQD_TRY(tune_ab_groups(ctx, t, 0, ab_launch_fp64, C));
     for (int v = 0; v < nvec; v++) {
         const double *Cv = C + (int64_t)v * N;
         double *Sv = S + (int64_t)v * N;
@@ -574,12 +579,12 @@ struct dav_work {
     double *Vb = nullptr, *Wb = nullptr, *X = nullptr, *R = nullptr, *Tmp = nullptr;
     double *G = nullptr, *evals = nullptr, *evecs = nullptr, *dots = nullptr, *partial = nullptr;
     double *phase = nullptr, *Yprev = nullptr, *Z = nullptr, *P = nullptr, *GZ = nullptr;
-    double *tn2 = nullptr;
+    double *tn2 = nullptr, *Eold = nullptr, *thold = nullptr;
     int64_t *idx = nullptr;
     int *rdev = nullptr;
     ~dav_work() {
         void *p[] = {Vb, Wb, X, R, Tmp, G, evals, evecs, dots, partial, phase, idx, Yprev, Z, P,
-                     GZ, tn2, rdev};
+                     GZ, tn2, Eold, thold, rdev};
         for (void *q : p)
             if (q) cudaFree(q);
     }
@@ -626,6 +631,8 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
     SQD_TRY(dalloc(ctx, &w.G, (int64_t)M * M));
     SQD_TRY(dalloc(ctx, &w.evals, M));
     SQD_TRY(dalloc(ctx, &w.evecs, (int64_t)M * M));
+    SQD_TRY(dalloc(ctx, &w.Eold, (int64_t)M * M));
+    SQD_TRY(dalloc(ctx, &w.thold, M));
     SQD_TRY(dalloc(ctx, &w.dots, M));
     SQD_TRY(dalloc(ctx, &w.partial, npart));
     SQD_TRY(dalloc(ctx, &w.phase, 3 * 4 * ctx->sm_count + 8));
@@ -718,10 +725,11 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
     std::vector<double> theta(M), theta_old(k, INFINITY), rn2(k), rn(k);
     int it = 0;
     int mprev = 0;  // rows of Yprev (0: no previous Ritz vectors yet)
+    int m_warm = 0;  // basis size of the previous eigensolve if the basis only grew since
     int status = SQD_OK;
     for (;;) {
         prof_begin(ctx, PROF_EIGH);
-        SQD_TRY(launch_jacobi_eigh(ctx, w.G, M, m, w.evals, w.evecs));
+        SQD_TRY(launch_jacobi_eigh(ctx, w.G, M, m, w.evals, w.evecs, m_warm, w.Eold, w.thold));
         prof_end(ctx, 0.0, 0.0);
         prof_begin(ctx, PROF_DAVIDSON);
         SQD_TRY(launch_ritz_block(ctx, w.Vb, w.Wb, N, m, w.evecs, w.evals, k, w.X, w.R, N,
@@ -772,11 +780,18 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
             // the current Ritz vectors are the first k basis vectors now
             SQD_TRY(launch_identity_cols(ctx, w.Yprev, m, k, M));
             mprev = m;
+            m_warm = 0;
         } else {
             SQD_CUDA(ctx, cudaMemcpy2DAsync(w.Yprev, sizeof(double) * M, w.evecs,
                                             sizeof(double) * m, sizeof(double) * m, k,
                                             cudaMemcpyDeviceToDevice, st));
             mprev = m;
+            // this eigensolve seeds the next one (the basis only grows)
+            SQD_CUDA(ctx, cudaMemcpyAsync(w.Eold, w.evecs, sizeof(double) * m * m,
+                                          cudaMemcpyDeviceToDevice, st));
+            SQD_CUDA(ctx, cudaMemcpyAsync(w.thold, w.evals, sizeof(double) * m,
+                                          cudaMemcpyDeviceToDevice, st));
+            m_warm = m;
         }
         const int m_old = m, b = (int)todo.size();
         prof_begin(ctx, PROF_DAVIDSON);

@@ -24,9 +24,18 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 
 #define JAC_MAX 112
 
+// Warm start (m_old > 0): the first m_old basis vectors are unchanged since
+// the previous solve, whose eigenvectors E_old (m_old x m_old, column-major)
+// and eigenvalues th_old are given.  The solver then works on
+// Q^T G Q with Q = diag(E_old, I): its leading block is diag(th_old) (the
+// previous solve converged), only the rows and columns of the appended
+// vectors couple, and far fewer sweeps are needed; the eigenvectors are
+// mapped back through Q at the end.
 __device__ __forceinline__ void jacobi_block(const double *__restrict__ G, int ldg, int m,
                                              double *__restrict__ evals,
-                                             double *__restrict__ evecs) {
+                                             double *__restrict__ evecs, int m_old = 0,
+                                             const double *__restrict__ E_old = nullptr,
+                                             const double *__restrict__ th_old = nullptr) {
     // A and Q live in dynamic shared memory, (M) x (M+1) doubles each
     extern __shared__ double jac_sh[];
     __shared__ double cs[JAC_MAX / 2], sn[JAC_MAX / 2];
@@ -43,7 +52,20 @@ __device__ __forceinline__ void jacobi_block(const double *__restrict__ G, int l
     for (int t = tid; t < M * M; t += nt) {
         int i = t / M, j = t % M;
         double v = 0.0;
-        if (i < m && j < m) v = (i <= j) ? G[i + (int64_t)j * ldg] : G[j + (int64_t)i * ldg];
+        if (i < m && j < m) {
+            if (i < m_old && j < m_old) {
+                v = (i == j) ? th_old[i] : 0.0;
+            } else if (i < m_old || j < m_old) {
+                // coupling of old Ritz vector q to appended vector c
+                const int q = min(i, j), c = max(i, j);
+                double sacc = 0.0;
+                for (int r = 0; r < m_old; r++)
+                    sacc = fma(E_old[r + (int64_t)q * m_old], G[r + (int64_t)c * ldg], sacc);
+                v = sacc;
+            } else {
+                v = (i <= j) ? G[i + (int64_t)j * ldg] : G[j + (int64_t)i * ldg];
+            }
+        }
         A(i, j) = v;
         Q(i, j) = (i == j) ? 1.0 : 0.0;
     }
@@ -131,8 +153,15 @@ __device__ __forceinline__ void jacobi_block(const double *__restrict__ G, int l
     }
     __syncthreads();
     for (int t = tid; t < m * m; t += nt) {
-        int i = t % m, j = t / m;  // evecs[i + j*m] = Q(i, order[j])
-        evecs[i + (int64_t)j * m] = Q(i, order[j]);
+        int i = t % m, j = t / m;  // evecs[i + j*m] = (diag(E_old, I) Q)(i, order[j])
+        double v;
+        if (i < m_old) {
+            v = 0.0;
+            for (int q = 0; q < m_old; q++) v = fma(E_old[i + (int64_t)q * m_old], Q(q, order[j]), v);
+        } else {
+            v = Q(i, order[j]);
+        }
+        evecs[i + (int64_t)j * m] = v;
     }
     for (int j = tid; j < m; j += nt) evals[j] = A(order[j], order[j]);
 }

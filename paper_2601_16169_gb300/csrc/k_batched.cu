@@ -599,7 +599,10 @@ static int set_groups(sqd_ctx *ctx, batched_plan &p, const std::vector<sqd_table
     std::vector<int64_t> pre{0};
     for (int b = 0; b < p.nprob; b++) {
         const sqd_tables *t = tabs[b];
-        int64_t ng = (int64_t)std::llround(std::max(1.0, t->ab.ngroups * scale));
+        // relative to the default split (the table's own split may be tuned)
+        const double base = t->ab.ngroups / (t->ab.scale > 0.0 ? t->ab.scale : 1.0);
+        int64_t ng = (int64_t)std::llround(std::max(1.0, base * scale));
+        if (ng > t->a.n) ng = std::max<int64_t>(1, t->a.n);
         std::vector<int64_t> g = alpha_groups(&t->a, ng);
         int64_t *dg = nullptr;
         SQD_TRY(plan_alloc(ctx, p, (void **)&dg, sizeof(int64_t) * g.size()));

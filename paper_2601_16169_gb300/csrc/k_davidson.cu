@@ -64,8 +64,42 @@ int launch_multidot(sqd_ctx *ctx, const double *A, int64_t lda, int m, const dou
 // out_j[n] = sum_i A_i[n] Y[i + j*ldy], j < k  (sub: out_j[n] -= that sum).
 // Each thread keeps 8 loads of A in flight (the basis does not fit in L2, so
 // the loop is bound by HBM latency otherwise) and up to 8 outputs in
-// registers; A is read once per group of 8 outputs.
+// registers; A is read once per group of 8 outputs.  The group width is a
+// template parameter: predicated-off FP64 instructions would still take
+// FP64 issue slots.
 #define CB_U 8
+template <int JN>
+__device__ __forceinline__ void combine_group(const double *__restrict__ A, int64_t lda, int m,
+                                              const double *__restrict__ Yj, int ldy,
+                                              double *__restrict__ out, int64_t ldo, int64_t p,
+                                              int sub) {
+    double acc[JN];
+#pragma unroll
+    for (int q = 0; q < JN; q++) acc[q] = 0.0;
+    int i = 0;
+    for (; i + CB_U <= m; i += CB_U) {
+        double a[CB_U];
+#pragma unroll
+        for (int u = 0; u < CB_U; u++) a[u] = A[(int64_t)(i + u) * lda + p];
+#pragma unroll
+        for (int u = 0; u < CB_U; u++) {
+#pragma unroll
+            for (int q = 0; q < JN; q++)
+                acc[q] = fma(a[u], __ldg(Yj + i + u + (int64_t)q * ldy), acc[q]);
+        }
+    }
+    for (; i < m; i++) {
+        const double a = A[(int64_t)i * lda + p];
+#pragma unroll
+        for (int q = 0; q < JN; q++) acc[q] = fma(a, __ldg(Yj + i + (int64_t)q * ldy), acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < JN; q++) {
+        double *o = out + (int64_t)q * ldo + p;
+        *o = sub ? *o - acc[q] : acc[q];
+    }
+}
+
 __global__ void __launch_bounds__(256) k_combine(const double *__restrict__ A, int64_t lda, int m,
                                                  const double *__restrict__ Y, int ldy, int k,
                                                  double *__restrict__ out, int64_t ldo, int64_t n,
@@ -73,35 +107,17 @@ __global__ void __launch_bounds__(256) k_combine(const double *__restrict__ A, i
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         for (int j0 = 0; j0 < k; j0 += 8) {
-            double acc[8];
-#pragma unroll
-            for (int q = 0; q < 8; q++) acc[q] = 0.0;
-            const int jn = min(8, k - j0);
             const double *Yj = Y + (int64_t)j0 * ldy;
-            int i = 0;
-            for (; i + CB_U <= m; i += CB_U) {
-                double a[CB_U];
-#pragma unroll
-                for (int u = 0; u < CB_U; u++) a[u] = A[(int64_t)(i + u) * lda + p];
-#pragma unroll
-                for (int u = 0; u < CB_U; u++) {
-#pragma unroll
-                    for (int q = 0; q < 8; q++)
-                        if (q < jn) acc[q] = fma(a[u], __ldg(Yj + i + u + (int64_t)q * ldy), acc[q]);
-                }
-            }
-            for (; i < m; i++) {
-                const double a = A[(int64_t)i * lda + p];
-#pragma unroll
-                for (int q = 0; q < 8; q++)
-                    if (q < jn) acc[q] = fma(a, __ldg(Yj + i + (int64_t)q * ldy), acc[q]);
-            }
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-                if (q < jn) {
-                    double *o = out + (int64_t)(j0 + q) * ldo + p;
-                    *o = sub ? *o - acc[q] : acc[q];
-                }
+            double *oj = out + (int64_t)j0 * ldo;
+            switch (min(8, k - j0)) {  // uniform across the grid
+                case 1: combine_group<1>(A, lda, m, Yj, ldy, oj, ldo, p, sub); break;
+                case 2: combine_group<2>(A, lda, m, Yj, ldy, oj, ldo, p, sub); break;
+                case 3: combine_group<3>(A, lda, m, Yj, ldy, oj, ldo, p, sub); break;
+                case 4: combine_group<4>(A, lda, m, Yj, ldy, oj, ldo, p, sub); break;
+                case 5: combine_group<5>(A, lda, m, Yj, ldy, oj, ldo, p, sub); break;
+                case 6: combine_group<6>(A, lda, m, Yj, ldy, oj, ldo, p, sub); break;
+                case 7: combine_group<7>(A, lda, m, Yj, ldy, oj, ldo, p, sub); break;
+                default: combine_group<8>(A, lda, m, Yj, ldy, oj, ldo, p, sub); break;
             }
         }
     }
@@ -261,7 +277,56 @@ int launch_block_dot(sqd_ctx *ctx, const double *A, int64_t lda, int m, const do
 // ------------------------------------------------- Ritz vectors, residuals --
 // For the k lowest Ritz pairs (theta_j, y_j): X_j = V y_j, R_j = W y_j -
 // theta_j X_j, and per-block partial sums of |R_j|^2 (partial[blk*k + j]).
-// V and W are read once per group of 8 roots.
+// V and W are read once per group of 8 roots (group width a template
+// parameter, as in k_combine).
+template <int JN>
+__device__ __forceinline__ void ritz_group(const double *__restrict__ V,
+                                           const double *__restrict__ W, int64_t ld, int m,
+                                           const double *__restrict__ Yj,
+                                           const double *__restrict__ thj, double *__restrict__ Xj,
+                                           double *__restrict__ Rj, int64_t n, double *ss) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double xa[JN], wa[JN];
+#pragma unroll
+        for (int q = 0; q < JN; q++) xa[q] = wa[q] = 0.0;
+        int i = 0;
+        for (; i + 4 <= m; i += 4) {
+            double v[4], w[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                v[u] = V[(int64_t)(i + u) * ld + p];
+                w[u] = W[(int64_t)(i + u) * ld + p];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+#pragma unroll
+                for (int q = 0; q < JN; q++) {
+                    const double y = __ldg(Yj + i + u + (int64_t)q * m);
+                    xa[q] = fma(v[u], y, xa[q]);
+                    wa[q] = fma(w[u], y, wa[q]);
+                }
+            }
+        }
+        for (; i < m; i++) {
+            const double v = V[(int64_t)i * ld + p], w = W[(int64_t)i * ld + p];
+#pragma unroll
+            for (int q = 0; q < JN; q++) {
+                const double y = __ldg(Yj + i + (int64_t)q * m);
+                xa[q] = fma(v, y, xa[q]);
+                wa[q] = fma(w, y, wa[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < JN; q++) {
+            const double r = fma(-__ldg(thj + q), xa[q], wa[q]);
+            Xj[(int64_t)q * ld + p] = xa[q];
+            Rj[(int64_t)q * ld + p] = r;
+            ss[q] = fma(r, r, ss[q]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(RED_THREADS)
     k_ritz_block(const double *__restrict__ V, const double *__restrict__ W, int64_t ld, int m,
                  const double *__restrict__ Y, const double *__restrict__ theta, int k,
@@ -273,51 +338,17 @@ __global__ void __launch_bounds__(RED_THREADS)
         double ss[8];
 #pragma unroll
         for (int q = 0; q < 8; q++) ss[q] = 0.0;
-        for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-             p += (int64_t)gridDim.x * blockDim.x) {
-            double xa[8], wa[8];
-#pragma unroll
-            for (int q = 0; q < 8; q++) xa[q] = wa[q] = 0.0;
-            int i = 0;
-            for (; i + 4 <= m; i += 4) {
-                double v[4], w[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    v[u] = V[(int64_t)(i + u) * ld + p];
-                    w[u] = W[(int64_t)(i + u) * ld + p];
-                }
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-#pragma unroll
-                    for (int q = 0; q < 8; q++) {
-                        if (q < jn) {
-                            const double y = __ldg(Y + i + u + (int64_t)(j0 + q) * m);
-                            xa[q] = fma(v[u], y, xa[q]);
-                            wa[q] = fma(w[u], y, wa[q]);
-                        }
-                    }
-                }
-            }
-            for (; i < m; i++) {
-                const double v = V[(int64_t)i * ld + p], w = W[(int64_t)i * ld + p];
-#pragma unroll
-                for (int q = 0; q < 8; q++) {
-                    if (q < jn) {
-                        const double y = __ldg(Y + i + (int64_t)(j0 + q) * m);
-                        xa[q] = fma(v, y, xa[q]);
-                        wa[q] = fma(w, y, wa[q]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-                if (q < jn) {
-                    const double r = fma(-__ldg(theta + j0 + q), xa[q], wa[q]);
-                    X[(int64_t)(j0 + q) * ld + p] = xa[q];
-                    R[(int64_t)(j0 + q) * ld + p] = r;
-                    ss[q] = fma(r, r, ss[q]);
-                }
-            }
+        const double *Yj = Y + (int64_t)j0 * m;
+        double *Xj = X + (int64_t)j0 * ld, *Rj = R + (int64_t)j0 * ld;
+        switch (jn) {  // uniform across the grid
+            case 1: ritz_group<1>(V, W, ld, m, Yj, theta + j0, Xj, Rj, n, ss); break;
+            case 2: ritz_group<2>(V, W, ld, m, Yj, theta + j0, Xj, Rj, n, ss); break;
+            case 3: ritz_group<3>(V, W, ld, m, Yj, theta + j0, Xj, Rj, n, ss); break;
+            case 4: ritz_group<4>(V, W, ld, m, Yj, theta + j0, Xj, Rj, n, ss); break;
+            case 5: ritz_group<5>(V, W, ld, m, Yj, theta + j0, Xj, Rj, n, ss); break;
+            case 6: ritz_group<6>(V, W, ld, m, Yj, theta + j0, Xj, Rj, n, ss); break;
+            case 7: ritz_group<7>(V, W, ld, m, Yj, theta + j0, Xj, Rj, n, ss); break;
+            default: ritz_group<8>(V, W, ld, m, Yj, theta + j0, Xj, Rj, n, ss); break;
         }
 #pragma unroll
         for (int q = 0; q < 8; q++) {
@@ -486,18 +517,22 @@ int launch_scale(sqd_ctx *ctx, double *x, int64_t n, const double *s_dev, int in
 
 __global__ void __launch_bounds__(1024) k_jacobi(const double *__restrict__ G, int ldg, int m,
                                                  double *__restrict__ evals,
-                                                 double *__restrict__ evecs) {
-    jacobi_block(G, ldg, m, evals, evecs);
+                                                 double *__restrict__ evecs, int m_old,
+                                                 const double *__restrict__ E_old,
+                                                 const double *__restrict__ th_old) {
+    jacobi_block(G, ldg, m, evals, evecs, m_old, E_old, th_old);
 }
 
 int launch_jacobi_eigh(sqd_ctx *ctx, const double *G, int ldg, int m, double *evals,
-                       double *evecs) {
+                       double *evecs, int m_old, const double *E_old, const double *th_old) {
     if (m < 1 || m > JAC_MAX) return sqd_fail(ctx, SQD_EINVAL, "subspace size %d out of range", m);
+    if (m_old < 0 || m_old > m || (m_old > 0 && (!E_old || !th_old)))
+        return sqd_fail(ctx, SQD_EINVAL, "bad warm start for the projected eigenproblem");
     int M = (m + 1) & ~1;
     size_t shm = sizeof(double) * 2 * (size_t)M * (M + 1);
     SQD_CUDA(ctx, cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(double) * 2 * JAC_MAX * (JAC_MAX + 1))));
-    k_jacobi<<<1, 1024, shm, ctx->stream>>>(G, ldg, m, evals, evecs);
+    k_jacobi<<<1, 1024, shm, ctx->stream>>>(G, ldg, m, evals, evecs, m_old, E_old, th_old);
     SQD_LAUNCHED(ctx);
     return SQD_OK;
 }

@@ -118,10 +118,42 @@ int launch_alpha_beta(sqd_ctx *ctx, const sqd_tables *t, const double *C, double
 }
 
 // Schedule for k_alpha_beta: beta chunks of at most AB_YW rows and AB_ECAP
-// entries; alpha groups of roughly equal single counts, enough of them to
-// give every SM several blocks.
+// entries; alpha groups of roughly equal single counts, about
+// scale * 16 blocks per SM in all (scale is tuned on the first sigma).
+int set_ab_groups(sqd_ctx *ctx, sqd_tables *t, double scale) {
+    const spin_tables *A = &t->a;
+    const int64_t target_blocks = (int64_t)(scale * 16.0 * ctx->sm_count + 0.5);
+    int64_t G = (target_blocks + t->ab.nchunks - 1) / t->ab.nchunks;
+    if (G > A->n) G = A->n;
+    if (G < 1) G = 1;
+    if (G > 65535) G = 65535;
+    const std::vector<int64_t> &ao = A->h_off1;
+    const int64_t total = ao[A->n];
+    std::vector<int64_t> groups{0};
+    int64_t r = 0;
+    for (int64_t g = 1; g < G; g++) {
+        const int64_t want = total * g / G;
+        while (r < A->n && ao[r] < want) r++;
+        if (r > groups.back()) groups.push_back(r);
+    }
+    groups.push_back(A->n);
+    if (t->ab.group_rows) {
+        SQD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // no launch still reads it
+        cudaFree(t->ab.group_rows);
+        t->ab.group_rows = nullptr;
+        t->bytes -= sizeof(int64_t) * (t->ab.ngroups + 1);
+    }
+    t->ab.ngroups = (int)groups.size() - 1;
+    SQD_CUDA(ctx, cudaMalloc((void **)&t->ab.group_rows, sizeof(int64_t) * groups.size()));
+    SQD_CUDA(ctx, cudaMemcpy(t->ab.group_rows, groups.data(), sizeof(int64_t) * groups.size(),
+                             cudaMemcpyHostToDevice));
+    t->bytes += sizeof(int64_t) * groups.size();
+    t->ab.scale = scale;
+    return SQD_OK;
+}
+
 int build_ab_schedule(sqd_ctx *ctx, sqd_tables *t) {
-    const spin_tables *A = &t->a, *B = t->b;
+    const spin_tables *B = t->b;
     std::vector<int64_t> chunks{0};
     const std::vector<int64_t> &bo = B->h_off1;
     int64_t y = 0;
@@ -132,32 +164,59 @@ int build_ab_schedule(sqd_ctx *ctx, sqd_tables *t) {
         chunks.push_back(y_end);
         y = y_end;
     }
-    int nchunks = (int)chunks.size() - 1;
-    int64_t target_blocks = 8LL * ctx->sm_count * 2;
-    int64_t G = (target_blocks + nchunks - 1) / nchunks;
-    if (G > A->n) G = A->n;
-    if (G < 1) G = 1;
-    if (G > 65535) G = 65535;
-    const std::vector<int64_t> &ao = A->h_off1;
-    int64_t total = ao[A->n];
-    std::vector<int64_t> groups{0};
-    int64_t r = 0;
-    for (int64_t g = 1; g < G; g++) {
-        int64_t want = total * g / G;
-        while (r < A->n && ao[r] < want) r++;
-        if (r > groups.back()) groups.push_back(r);
-    }
-    groups.push_back(A->n);
-    t->ab.nchunks = nchunks;
-    t->ab.ngroups = (int)groups.size() - 1;
+    t->ab.nchunks = (int)chunks.size() - 1;
     SQD_CUDA(ctx, cudaMalloc((void **)&t->ab.chunk_rows, sizeof(int64_t) * chunks.size()));
-    SQD_CUDA(ctx, cudaMalloc((void **)&t->ab.group_rows, sizeof(int64_t) * groups.size()));
     SQD_CUDA(ctx, cudaMemcpy(t->ab.chunk_rows, chunks.data(), sizeof(int64_t) * chunks.size(),
                              cudaMemcpyHostToDevice));
-    SQD_CUDA(ctx, cudaMemcpy(t->ab.group_rows, groups.data(), sizeof(int64_t) * groups.size(),
-                             cudaMemcpyHostToDevice));
-    t->bytes += sizeof(int64_t) * (chunks.size() + groups.size());
-    return SQD_OK;
+    t->bytes += sizeof(int64_t) * chunks.size();
+    return set_ab_groups(ctx, t, 1.0);
+}
+
+// Pick the alpha-group scale of sigma mode `mode` by timing one paired-singles
+// launch per candidate on the caller's vector (output to scratch), once per
+// table and mode; afterwards only re-applies the chosen schedule.
+int tune_ab_groups(sqd_ctx *ctx, sqd_tables *t, int mode,
+                   int (*launch)(sqd_ctx *, sqd_tables *, const void *, double *),
+                   const void *C) {
+    if (t->a.nnz1 == 0 || t->b->nnz1 == 0) return SQD_OK;
+    if (t->ab.best[mode] > 0.0) {
+        if (t->ab.scale != t->ab.best[mode]) SQD_TRY(set_ab_groups(ctx, t, t->ab.best[mode]));
+        return SQD_OK;
+    }
+    const double cand[] = {0.125, 0.25, 0.5, 1.0};
+    const int64_t N = t->a.n * t->b->n;
+    cudaEvent_t e0, e1;
+    SQD_CUDA(ctx, cudaEventCreate(&e0));
+    SQD_CUDA(ctx, cudaEventCreate(&e1));
+    double best = 1.0;
+    float best_ms = INFINITY;
+    int rc = SQD_OK;
+    for (double sc : cand) {
+        if ((rc = set_ab_groups(ctx, t, sc)) != SQD_OK) break;
+        if (cudaMemsetAsync(t->scratch_s, 0, sizeof(double) * N, ctx->stream) != cudaSuccess) {
+            rc = sqd_fail(ctx, SQD_ECUDA, "memset failed");
+            break;
+        }
+        cudaEventRecord(e0, ctx->stream);
+        if ((rc = launch(ctx, t, C, t->scratch_s)) != SQD_OK) break;
+        cudaEventRecord(e1, ctx->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = sqd_fail(ctx, SQD_ECUDA, "paired-singles tuning launch failed: %s",
+                          cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = sc;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != SQD_OK) return rc;
+    t->ab.best[mode] = best;
+    return set_ab_groups(ctx, t, best);
 }
 
 // ------------------------------------------------------------ transpose --

@@ -264,6 +264,21 @@ static ss_df_args make_df_args(const spin_tables *R, const spin_tables *Cc, int6
     return a;
 }
 
+// the paired-singles term on float-pair C, added into S
+static int launch_alpha_beta_df(sqd_ctx *ctx, sqd_tables *t, const void *Cv, double *S) {
+    const spin_tables *A = &t->a, *B = t->b;
+    if (A->nnz1 == 0 || B->nnz1 == 0) return SQD_OK;
+    const size_t shm = sizeof(float2) * 2 * AB_NA * AB_YW;
+    SQD_CUDA(ctx, cudaFuncSetAttribute(k_alpha_beta_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)shm));
+    k_alpha_beta_df<<<dim3((unsigned)t->ab.nchunks, (unsigned)t->ab.ngroups), AB_THREADS, shm,
+                      ctx->stream>>>(B->n, t->norb * t->norb, A->off1, A->tgt1, A->pq1, A->sgn1,
+                                     B->off1, B->tgt1, B->pq1, B->sgn1, t->ab.chunk_rows,
+                                     t->ab.group_rows, (const float2 *)Cv, S, t->Vf);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
 // one vector: split, alpha side + diagonal, alpha-beta, beta side on C^T
 int sigma_df_one(sqd_ctx *ctx, sqd_tables *t, const double *Cv, double *Sv, double f_a,
                  double f_b, double f_ab) {
@@ -281,15 +296,9 @@ int sigma_df_one(sqd_ctx *ctx, sqd_tables *t, const double *Cv, double *Sv, doub
     SQD_LAUNCHED(ctx);
     prof_end(ctx, f_a, 3 * vb);
     if (A->nnz1 > 0 && B->nnz1 > 0) {
+        SQD_TRY(tune_ab_groups(ctx, t, 1, launch_alpha_beta_df, Cf));
         prof_begin(ctx, PROF_ALPHA_BETA);
-        const size_t shm = sizeof(float2) * 2 * AB_NA * AB_YW;
-        SQD_CUDA(ctx, cudaFuncSetAttribute(k_alpha_beta_df,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        k_alpha_beta_df<<<dim3((unsigned)t->ab.nchunks, (unsigned)t->ab.ngroups), AB_THREADS, shm,
-                          ctx->stream>>>(nb, t->norb * t->norb, A->off1, A->tgt1, A->pq1,
-                                         A->sgn1, B->off1, B->tgt1, B->pq1, B->sgn1,
-                                         t->ab.chunk_rows, t->ab.group_rows, Cf, Sv, t->Vf);
-        SQD_LAUNCHED(ctx);
+        SQD_TRY(launch_alpha_beta_df(ctx, t, Cf, Sv));
         prof_end(ctx, f_ab, 3 * vb);
     }
     // C^T of the float pairs (moved as 8-byte words), beta side, add back

@@ -94,6 +94,8 @@ struct ab_schedule {
     // alpha row groups: [grp[g], grp[g+1])
     int ngroups = 0;
     int64_t *group_rows = nullptr;  // device, ngroups+1
+    double scale = 0.0;             // blocks = scale * 16 per SM (current groups)
+    double best[2] = {0.0, 0.0};    // tuned scale per sigma mode (0: not yet)
 };
 
 struct sqd_tables {
@@ -196,6 +198,9 @@ int launch_same_spin(sqd_ctx *, const spin_tables *rows, const spin_tables *cols
                      int64_t nrows, int64_t ncols, const double *C, double *S,
                      const double *diag);
 int launch_alpha_beta(sqd_ctx *, const sqd_tables *t, const double *C, double *S);
+int set_ab_groups(sqd_ctx *, sqd_tables *t, double scale);
+int tune_ab_groups(sqd_ctx *, sqd_tables *t, int mode,
+                   int (*launch)(sqd_ctx *, sqd_tables *, const void *, double *), const void *C);
 int launch_transpose(sqd_ctx *, const double *in, double *out, int64_t rows, int64_t cols,
                      bool add);
 
@@ -226,8 +231,9 @@ int launch_precondition_norm(sqd_ctx *, const double *R, const double *diag, dou
                              double floor_, int64_t n, double *T, double *partial,
                              double *norm2);
 int launch_scale(sqd_ctx *, double *x, int64_t n, const double *s_dev, int invert_sqrt);
-int launch_jacobi_eigh(sqd_ctx *, const double *G, int ldg, int m, double *evals,
-                       double *evecs);
+int launch_jacobi_eigh(sqd_ctx *, const double *G, int ldg, int m, double *evals, double *evecs,
+                       int m_old = 0, const double *E_old = nullptr,
+                       const double *th_old = nullptr);
 int launch_argmin_k(sqd_ctx *, const double *d, int64_t n, int k, int64_t *idx_dev);
 int launch_set_unit(sqd_ctx *, double *V, int64_t ld, int k, const int64_t *idx_dev);
 int launch_fix_phase(sqd_ctx *, double *X, int64_t ld, int k, int64_t n, double *work_dev);
