@@ -235,7 +235,7 @@ int sqd_build_strings(sqd_ctx *ctx, const uint64_t *d_raw, int64_t n_raw, int no
 // ----------------------------------------------------------- a2-a4 ------
 
 static void free_spin(spin_tables *s) {
-    void *ptrs[] = {s->str,  s->off1, s->tgt1,   s->pq1, s->sgn1, s->val1,  s->off2,
+    void *ptrs[] = {s->str,  s->off1, s->tgt1,   s->pq1, s->sgn1, s->val1,  s->src1, s->off2,
                     s->tgt2, s->orb2, s->sgn2,   s->val2, s->energy, s->W, s->u,
                     s->val1f, s->val2f, s->Wf};
     for (void *p : ptrs)
@@ -581,10 +581,10 @@ struct dav_work {
     double *phase = nullptr, *Yprev = nullptr, *Z = nullptr, *P = nullptr, *GZ = nullptr;
     double *tn2 = nullptr, *Eold = nullptr, *thold = nullptr;
     int64_t *idx = nullptr;
-    int *rdev = nullptr;
+    int *rdev = nullptr, *sel = nullptr;
     ~dav_work() {
         void *p[] = {Vb, Wb, X, R, Tmp, G, evals, evecs, dots, partial, phase, idx, Yprev, Z, P,
-                     GZ, tn2, Eold, thold, rdev};
+                     GZ, tn2, Eold, thold, rdev, sel};
         for (void *q : p)
             if (q) cudaFree(q);
     }
@@ -628,6 +628,7 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
     SQD_TRY(dalloc(ctx, &w.GZ, (int64_t)M * kr));
     SQD_TRY(dalloc(ctx, &w.tn2, k));
     SQD_TRY(dalloc(ctx, &w.rdev, 1));
+    SQD_TRY(dalloc(ctx, &w.sel, k));
     SQD_TRY(dalloc(ctx, &w.G, (int64_t)M * M));
     SQD_TRY(dalloc(ctx, &w.evals, M));
     SQD_TRY(dalloc(ctx, &w.evecs, (int64_t)M * M));
@@ -722,41 +723,81 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
     SQD_TRY(apply_h(w.Vb, w.Wb, m));
     SQD_TRY(g_cols(m, 0, m));
 
-    std::vector<double> theta(M), theta_old(k, INFINITY), rn2(k), rn(k);
+    // Soft locking: a root that met both tests is locked and its Ritz vector
+    // and residual are no longer formed; once every root is locked, one
+    // iteration forms all of them and the solve ends only if every root
+    // passes there (failing roots are unlocked and the solve goes on).
+    // Energy test: the change of theta_j across the last growth of the basis.
+    std::vector<double> theta(M), theta_old(k, INFINITY), dth(k, INFINITY), rn2(k), rn(k, INFINITY);
+    std::vector<char> locked(k, 0);
+    std::vector<int> sel;
     int it = 0;
     int mprev = 0;  // rows of Yprev (0: no previous Ritz vectors yet)
     int m_warm = 0;  // basis size of the previous eigensolve if the basis only grew since
+    bool grown = true;  // basis changed since the previous eigensolve
     int status = SQD_OK;
+    // Ritz vectors and residual norms of every root from the current eigensolve
+    auto ritz_all = [&]() -> int {
+        sel.clear();
+        for (int j = 0; j < k; j++) sel.push_back(j);
+        SQD_CUDA(ctx, cudaMemcpyAsync(w.sel, sel.data(), sizeof(int) * k, cudaMemcpyHostToDevice,
+                                      st));
+        SQD_TRY(launch_ritz_block(ctx, w.Vb, w.Wb, N, m, w.evecs, w.evals, w.sel, k, w.X, w.R, N,
+                                  w.partial, nbr, w.dots));
+        SQD_CUDA(ctx, cudaMemcpyAsync(rn2.data(), w.dots, sizeof(double) * k,
+                                      cudaMemcpyDeviceToHost, st));
+        SQD_CUDA(ctx, cudaMemcpyAsync(theta.data(), w.evals, sizeof(double) * m,
+                                      cudaMemcpyDeviceToHost, st));
+        SQD_CUDA(ctx, cudaStreamSynchronize(st));
+        for (int j = 0; j < k; j++) rn[j] = std::sqrt(std::max(rn2[j], 0.0));
+        return SQD_OK;
+    };
     for (;;) {
         prof_begin(ctx, PROF_EIGH);
         SQD_TRY(launch_jacobi_eigh(ctx, w.G, M, m, w.evals, w.evecs, m_warm, w.Eold, w.thold));
         prof_end(ctx, 0.0, 0.0);
+        sel.clear();
+        for (int j = 0; j < k; j++)
+            if (!locked[j]) sel.push_back(j);
+        const bool full = sel.empty();
+        if (full)
+            for (int j = 0; j < k; j++) sel.push_back(j);
+        const int ks = (int)sel.size();
+        SQD_CUDA(ctx, cudaMemcpyAsync(w.sel, sel.data(), sizeof(int) * ks, cudaMemcpyHostToDevice,
+                                      st));
         prof_begin(ctx, PROF_DAVIDSON);
-        SQD_TRY(launch_ritz_block(ctx, w.Vb, w.Wb, N, m, w.evecs, w.evals, k, w.X, w.R, N,
+        SQD_TRY(launch_ritz_block(ctx, w.Vb, w.Wb, N, m, w.evecs, w.evals, w.sel, ks, w.X, w.R, N,
                                   w.partial, nbr, w.dots));
-        prof_end(ctx, 4.0 * m * k * dN + 2.0 * k * dN, 8.0 * (2.0 * m + 2.0 * k) * dN);
+        prof_end(ctx, 4.0 * m * ks * dN + 2.0 * ks * dN, 8.0 * (2.0 * m + 2.0 * ks) * dN);
         SQD_CUDA(ctx, cudaMemcpyAsync(theta.data(), w.evals, sizeof(double) * m,
                                       cudaMemcpyDeviceToHost, st));
-        SQD_CUDA(ctx, cudaMemcpyAsync(rn2.data(), w.dots, sizeof(double) * k,
+        SQD_CUDA(ctx, cudaMemcpyAsync(rn2.data(), w.dots, sizeof(double) * ks,
                                       cudaMemcpyDeviceToHost, st));
         SQD_CUDA(ctx, cudaStreamSynchronize(st));
+        if (grown)
+            for (int j = 0; j < k; j++) dth[j] = std::fabs(theta[j] - theta_old[j]);
+        for (int j = 0; j < k; j++) theta_old[j] = theta[j];
         bool all = true;
         std::vector<int> todo;
-        for (int j = 0; j < k; j++) {
-            rn[j] = std::sqrt(std::max(rn2[j], 0.0));
-            bool c = rn[j] <= o->tol_residual && std::fabs(theta[j] - theta_old[j]) <= o->tol_energy;
+        for (int q = 0; q < ks; q++) {
+            const int j = sel[q];
+            rn[j] = std::sqrt(std::max(rn2[q], 0.0));
+            const bool c = rn[j] <= o->tol_residual && dth[j] <= o->tol_energy;
+            locked[j] = c ? 1 : 0;
             if (!c) {
                 all = false;
                 todo.push_back(j);
             }
         }
-        if (all) break;
+        if (full && all) break;
         if (it >= o->max_iter) {
             status = SQD_ENOTCONVERGED;
+            if (!full) SQD_TRY(ritz_all());
             break;
         }
         it++;
-        for (int j = 0; j < k; j++) theta_old[j] = theta[j];
+        grown = !todo.empty();
+        if (todo.empty()) continue;  // every root locked: check them all next
         if (m + (int)todo.size() > M) {
             // restart (GD+k): the 2k lowest Ritz vectors plus the k Ritz vectors
             // of the previous iteration, orthonormalised against them
@@ -806,6 +847,8 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
         SQD_TRY(orthonormalize_block(m_old, b, true, &nacc));
         m = m_old + nacc;
         if (nacc == 0) {
+            SQD_TRY(launch_jacobi_eigh(ctx, w.G, M, m, w.evals, w.evecs));
+            SQD_TRY(ritz_all());
             bool res_ok = true;
             for (int j = 0; j < k; j++) res_ok = res_ok && rn[j] <= o->tol_residual;
             if (!res_ok) status = SQD_EBREAKDOWN;

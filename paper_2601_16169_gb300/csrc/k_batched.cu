@@ -175,7 +175,22 @@ __global__ void __launch_bounds__(BV_THREADS) kb_ritz(const bdesc *__restrict__ 
     double ss = 0.0;
     for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) {
         double x = 0.0, w = 0.0;
-        for (int i = 0; i < m; i++) {
+        int i = 0;
+        for (; i + 4 <= m; i += 4) {  // 8 loads in flight
+            double v[4], ww[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                v[u] = d.V[(int64_t)(i + u) * d.N + n];
+                ww[u] = d.W[(int64_t)(i + u) * d.N + n];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const double y = d.evecs[i + u];
+                x = fma(v[u], y, x);
+                w = fma(ww[u], y, w);
+            }
+        }
+        for (; i < m; i++) {
             const double y = d.evecs[i];
             x = fma(d.V[(int64_t)i * d.N + n], y, x);
             w = fma(d.W[(int64_t)i * d.N + n], y, w);
@@ -332,7 +347,22 @@ __global__ void __launch_bounds__(BV_THREADS) kb_gram(const bdesc *__restrict__ 
     const int m = st.m;
     const double *x = (mode == 2) ? d.W + (int64_t)(m - 1) * d.N : d.V + (int64_t)m * d.N;
     const int cnt = (mode == 1) ? 1 : m;
-    for (int i = 0; i < cnt; i++) {
+    int i = 0;
+    for (; i + 4 <= cnt; i += 4) {  // four basis vectors per pass over the slice
+        const double *a0 = d.V + (int64_t)i * d.N;
+        double s[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) {
+            const double xn = x[n];
+#pragma unroll
+            for (int u = 0; u < 4; u++) s[u] = fma(a0[(int64_t)u * d.N + n], xn, s[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const double t = block_sum(s[u], red);
+            if (threadIdx.x == 0) d.partial[(int64_t)(i + u) * d.nsl + sl.s] = t;
+        }
+    }
+    for (; i < cnt; i++) {
         const double *a = d.V + (int64_t)(mode == 1 ? m : i) * d.N;
         double s = 0.0;
         for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) s = fma(a[n], x[n], s);
@@ -371,7 +401,15 @@ __global__ void __launch_bounds__(BV_THREADS) kb_project_out(const bdesc *__rest
     double *t = d.V + (int64_t)m * d.N;
     for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) {
         double s = 0.0;
-        for (int i = 0; i < m; i++) s = fma(d.V[(int64_t)i * d.N + n], d.coef[i], s);
+        int i = 0;
+        for (; i + 8 <= m; i += 8) {  // 8 loads in flight
+            double a[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) a[u] = d.V[(int64_t)(i + u) * d.N + n];
+#pragma unroll
+            for (int u = 0; u < 8; u++) s = fma(a[u], d.coef[i + u], s);
+        }
+        for (; i < m; i++) s = fma(d.V[(int64_t)i * d.N + n], d.coef[i], s);
         t[n] -= s;
     }
 }

@@ -275,16 +275,24 @@ int launch_block_dot(sqd_ctx *ctx, const double *A, int64_t lda, int m, const do
 }
 
 // ------------------------------------------------- Ritz vectors, residuals --
-// For the k lowest Ritz pairs (theta_j, y_j): X_j = V y_j, R_j = W y_j -
-// theta_j X_j, and per-block partial sums of |R_j|^2 (partial[blk*k + j]).
-// V and W are read once per group of 8 roots (group width a template
-// parameter, as in k_combine).
+// For the selected Ritz pairs j = sel[q], q < ks (theta_j, y_j = column j of
+// Y, ld m): X_j = V y_j, R_j = W y_j - theta_j X_j, and per-block partial
+// sums of |R_j|^2 (partial[blk*ks + q]).  V and W are read once per group of
+// 8 selected roots (group width a template parameter, as in k_combine).
 template <int JN>
 __device__ __forceinline__ void ritz_group(const double *__restrict__ V,
                                            const double *__restrict__ W, int64_t ld, int m,
-                                           const double *__restrict__ Yj,
-                                           const double *__restrict__ thj, double *__restrict__ Xj,
-                                           double *__restrict__ Rj, int64_t n, double *ss) {
+                                           const double *__restrict__ Y,
+                                           const double *__restrict__ theta,
+                                           const int *__restrict__ selq, double *__restrict__ X,
+                                           double *__restrict__ R, int64_t n, double *ss) {
+    int jj[JN];
+    double th[JN];
+#pragma unroll
+    for (int q = 0; q < JN; q++) {
+        jj[q] = __ldg(selq + q);
+        th[q] = __ldg(theta + jj[q]);
+    }
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         double xa[JN], wa[JN];
@@ -302,7 +310,7 @@ __device__ __forceinline__ void ritz_group(const double *__restrict__ V,
             for (int u = 0; u < 4; u++) {
 #pragma unroll
                 for (int q = 0; q < JN; q++) {
-                    const double y = __ldg(Yj + i + u + (int64_t)q * m);
+                    const double y = __ldg(Y + i + u + (int64_t)jj[q] * m);
                     xa[q] = fma(v[u], y, xa[q]);
                     wa[q] = fma(w[u], y, wa[q]);
                 }
@@ -312,16 +320,16 @@ __device__ __forceinline__ void ritz_group(const double *__restrict__ V,
             const double v = V[(int64_t)i * ld + p], w = W[(int64_t)i * ld + p];
 #pragma unroll
             for (int q = 0; q < JN; q++) {
-                const double y = __ldg(Yj + i + (int64_t)q * m);
+                const double y = __ldg(Y + i + (int64_t)jj[q] * m);
                 xa[q] = fma(v, y, xa[q]);
                 wa[q] = fma(w, y, wa[q]);
             }
         }
 #pragma unroll
         for (int q = 0; q < JN; q++) {
-            const double r = fma(-__ldg(thj + q), xa[q], wa[q]);
-            Xj[(int64_t)q * ld + p] = xa[q];
-            Rj[(int64_t)q * ld + p] = r;
+            const double r = fma(-th[q], xa[q], wa[q]);
+            X[(int64_t)jj[q] * ld + p] = xa[q];
+            R[(int64_t)jj[q] * ld + p] = r;
             ss[q] = fma(r, r, ss[q]);
         }
     }
@@ -329,32 +337,31 @@ __device__ __forceinline__ void ritz_group(const double *__restrict__ V,
 
 __global__ void __launch_bounds__(RED_THREADS)
     k_ritz_block(const double *__restrict__ V, const double *__restrict__ W, int64_t ld, int m,
-                 const double *__restrict__ Y, const double *__restrict__ theta, int k,
-                 double *__restrict__ X, double *__restrict__ R, int64_t n,
-                 double *__restrict__ partial) {
+                 const double *__restrict__ Y, const double *__restrict__ theta,
+                 const int *__restrict__ sel, int ks, double *__restrict__ X,
+                 double *__restrict__ R, int64_t n, double *__restrict__ partial) {
     __shared__ double red[32];
-    for (int j0 = 0; j0 < k; j0 += 8) {
-        const int jn = min(8, k - j0);
+    for (int j0 = 0; j0 < ks; j0 += 8) {
+        const int jn = min(8, ks - j0);
         double ss[8];
 #pragma unroll
         for (int q = 0; q < 8; q++) ss[q] = 0.0;
-        const double *Yj = Y + (int64_t)j0 * m;
-        double *Xj = X + (int64_t)j0 * ld, *Rj = R + (int64_t)j0 * ld;
+        const int *sq = sel + j0;
         switch (jn) {  // uniform across the grid
-            case 1: ritz_group<1>(V, W, ld, m, Yj, theta + j0, Xj, Rj, n, ss); break;
-            case 2: ritz_group<2>(V, W, ld, m, Yj, theta + j0, Xj, Rj, n, ss); break;
-            case 3: ritz_group<3>(V, W, ld, m, Yj, theta + j0, Xj, Rj, n, ss); break;
-            case 4: ritz_group<4>(V, W, ld, m, Yj, theta + j0, Xj, Rj, n, ss); break;
-            case 5: ritz_group<5>(V, W, ld, m, Yj, theta + j0, Xj, Rj, n, ss); break;
-            case 6: ritz_group<6>(V, W, ld, m, Yj, theta + j0, Xj, Rj, n, ss); break;
-            case 7: ritz_group<7>(V, W, ld, m, Yj, theta + j0, Xj, Rj, n, ss); break;
-            default: ritz_group<8>(V, W, ld, m, Yj, theta + j0, Xj, Rj, n, ss); break;
+            case 1: ritz_group<1>(V, W, ld, m, Y, theta, sq, X, R, n, ss); break;
+            case 2: ritz_group<2>(V, W, ld, m, Y, theta, sq, X, R, n, ss); break;
+            case 3: ritz_group<3>(V, W, ld, m, Y, theta, sq, X, R, n, ss); break;
+            case 4: ritz_group<4>(V, W, ld, m, Y, theta, sq, X, R, n, ss); break;
+            case 5: ritz_group<5>(V, W, ld, m, Y, theta, sq, X, R, n, ss); break;
+            case 6: ritz_group<6>(V, W, ld, m, Y, theta, sq, X, R, n, ss); break;
+            case 7: ritz_group<7>(V, W, ld, m, Y, theta, sq, X, R, n, ss); break;
+            default: ritz_group<8>(V, W, ld, m, Y, theta, sq, X, R, n, ss); break;
         }
 #pragma unroll
         for (int q = 0; q < 8; q++) {
             if (q < jn) {  // uniform across the block
                 const double t = block_sum(ss[q], red);
-                if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * k + j0 + q] = t;
+                if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * ks + j0 + q] = t;
             }
         }
     }
@@ -369,14 +376,15 @@ __global__ void k_ritz_final(const double *__restrict__ partial, int nblk, int k
     out[j] = s;
 }
 
+// sel: device array of ks root indices; rnorm2[q] = |R_sel[q]|^2
 int launch_ritz_block(sqd_ctx *ctx, const double *V, const double *W, int64_t ld, int m,
-                      const double *Y, const double *theta, int k, double *X, double *R,
-                      int64_t n, double *partial, int nblk, double *rnorm2) {
-    if (k == 0 || n == 0) return SQD_OK;
-    k_ritz_block<<<nblk, RED_THREADS, 0, ctx->stream>>>(V, W, ld, m, Y, theta, k, X, R, n,
+                      const double *Y, const double *theta, const int *sel, int ks, double *X,
+                      double *R, int64_t n, double *partial, int nblk, double *rnorm2) {
+    if (ks == 0 || n == 0) return SQD_OK;
+    k_ritz_block<<<nblk, RED_THREADS, 0, ctx->stream>>>(V, W, ld, m, Y, theta, sel, ks, X, R, n,
                                                         partial);
     SQD_LAUNCHED(ctx);
-    k_ritz_final<<<(k + 63) / 64, 64, 0, ctx->stream>>>(partial, nblk, k, rnorm2);
+    k_ritz_final<<<(ks + 63) / 64, 64, 0, ctx->stream>>>(partial, nblk, ks, rnorm2);
     SQD_LAUNCHED(ctx);
     return SQD_OK;
 }

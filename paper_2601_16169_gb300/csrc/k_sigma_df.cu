@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256) k_same_spin_df(ss_df_args a) {
 
 __global__ void __launch_bounds__(AB_THREADS, 2)
     k_alpha_beta_df(int64_t nb, int norb2, const int64_t *__restrict__ a_off,
-                    const int32_t *__restrict__ a_tgt, const uint16_t *__restrict__ a_pq,
+                    const int32_t *__restrict__ a_src, const int32_t *__restrict__ a_tgt, const uint16_t *__restrict__ a_pq,
                     const int8_t *__restrict__ a_sgn, const int64_t *__restrict__ b_off,
                     const int32_t *__restrict__ b_tgt, const uint16_t *__restrict__ b_pq,
                     const int8_t *__restrict__ b_sgn, const int64_t *__restrict__ chunk_rows,
@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(AB_THREADS, 2)
     float2(*slab)[AB_NA][AB_YW] = reinterpret_cast<float2(*)[AB_NA][AB_YW]>(abdf_dyn);
     __shared__ int64_t sh_vrow[2][AB_NA];
     __shared__ uint32_t sh_sa[2][AB_NA];
+    __shared__ int64_t sh_row[2][AB_NA];
     __shared__ int64_t sh_off[AB_YW + 1];
 
     const int tid = threadIdx.x;
@@ -156,36 +157,46 @@ __global__ void __launch_bounds__(AB_THREADS, 2)
         ae[k] = 0.f;
     }
 
-    const int64_t g1 = group_rows[blockIdx.y + 1];
-    auto stage = [&](const ab_item &it, int buf) {
-        const int nbat = (int)min((int64_t)AB_NA, it.a1 - it.ab);
+    const int64_t g0 = group_rows[blockIdx.y], g1 = group_rows[blockIdx.y + 1];
+    const int64_t xs = a_off[g0], xe = a_off[g1];
+    auto stage = [&](int64_t x0, int buf) {
+        const int nbat = (int)min((int64_t)AB_NA, xe - x0);
         if (tid < nbat) {
-            sh_vrow[buf][tid] = (int64_t)a_pq[it.ab + tid] * norb2;
-            sh_sa[buf][tid] = (a_sgn[it.ab + tid] < 0) ? 1u : 0u;
+            const int64_t x = x0 + tid;
+            sh_vrow[buf][tid] = (int64_t)a_pq[x] * norb2;
+            sh_sa[buf][tid] = (a_sgn[x] < 0) ? 1u : 0u;
+            sh_row[buf][tid] = a_src[x];
         }
         for (int idx = tid; idx < nbat * width; idx += AB_THREADS) {
             const int aa = idx / width, j = idx - aa * width;
-            cp_async8(&slab[buf][aa][j], C + (int64_t)a_tgt[it.ab + aa] * nb + y0 + j);
+            cp_async8(&slab[buf][aa][j], C + (int64_t)a_tgt[x0 + aa] * nb + y0 + j);
         }
         cp_async_commit();
     };
+    auto flush = [&](int64_t row) {
+#pragma unroll
+        for (int k = 0; k < AB_EPT; k++) {
+            if (ib[k] >= 0) atomicAdd(&S[row * nb + ib[k]], df_value(as[k], ae[k]));
+            as[k] = 0.f;
+            ae[k] = 0.f;
+        }
+    };
 
-    ab_item cur;
-    cur.ia = group_rows[blockIdx.y] - 1;
-    cur.ab = 0;
-    cur.a1 = 0;
-    bool have = ab_next(a_off, g1, cur);
-    if (have) stage(cur, 0);
+    if (xs < xe) stage(xs, 0);
     int buf = 0;
-    while (have) {
-        ab_item nxt = cur;
-        const bool more = ab_next(a_off, g1, nxt);
-        if (more) stage(nxt, buf ^ 1);
+    int64_t row_cur = -1;  // alpha row of the sums held (uniform across the block)
+    for (int64_t xb = xs; xb < xe; xb += AB_NA) {
+        if (xb + AB_NA < xe) stage(xb + AB_NA, buf ^ 1);
         else cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
-        const int nbat = (int)min((int64_t)AB_NA, cur.a1 - cur.ab);
+        const int nbat = (int)min((int64_t)AB_NA, xe - xb);
         for (int ai = 0; ai < nbat; ai++) {
+            const int64_t row = sh_row[buf][ai];
+            if (row != row_cur) {
+                if (row_cur >= 0) flush(row_cur);
+                row_cur = row;
+            }
             const float2 *vr = V + sh_vrow[buf][ai];
             const uint32_t sa = sh_sa[buf][ai] << 31;
             const float2 *sl = slab[buf][ai];
@@ -197,19 +208,10 @@ __global__ void __launch_bounds__(AB_THREADS, 2)
                 df_mac(v.x, v.y, c.x, c.y, as[k], ae[k]);
             }
         }
-        if (cur.ab + AB_NA >= cur.a1) {
-#pragma unroll
-            for (int k = 0; k < AB_EPT; k++) {
-                if (ib[k] >= 0) atomicAdd(&S[cur.ia * nb + ib[k]], df_value(as[k], ae[k]));
-                as[k] = 0.f;
-                ae[k] = 0.f;
-            }
-        }
         __syncthreads();
-        cur = nxt;
-        have = more;
         buf ^= 1;
     }
+    if (row_cur >= 0) flush(row_cur);
     cp_async_wait<0>();
 }
 
@@ -272,7 +274,8 @@ static int launch_alpha_beta_df(sqd_ctx *ctx, sqd_tables *t, const void *Cv, dou
     SQD_CUDA(ctx, cudaFuncSetAttribute(k_alpha_beta_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)shm));
     k_alpha_beta_df<<<dim3((unsigned)t->ab.nchunks, (unsigned)t->ab.ngroups), AB_THREADS, shm,
-                      ctx->stream>>>(B->n, t->norb * t->norb, A->off1, A->tgt1, A->pq1, A->sgn1,
+                      ctx->stream>>>(B->n, t->norb * t->norb, A->off1, A->src1, A->tgt1, A->pq1,
+                                     A->sgn1,
                                      B->off1, B->tgt1, B->pq1, B->sgn1, t->ab.chunk_rows,
                                      t->ab.group_rows, (const float2 *)Cv, S, t->Vf);
     SQD_LAUNCHED(ctx);

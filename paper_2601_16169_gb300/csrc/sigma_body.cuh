@@ -26,6 +26,7 @@ struct ab_args {
     int64_t nb;
     int norb2;
     const int64_t *a_off;
+    const int32_t *a_src;
     const int32_t *a_tgt;
     const uint16_t *a_pq;
     const int8_t *a_sgn;
@@ -58,29 +59,12 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Work items of a block are (alpha row, batch of AB_NA alpha singles) pairs
-// over the rows of its group that have singles, in order.  The slabs of
-// item i+1 are copied (cp.async) while item i is computed.
-struct ab_item {
-    int64_t ia, ab, a1;  // row, first single of the batch, end of the row's singles
-};
+// The work of a block is the alpha singles of its row group, the contiguous
+// range [a_off[g0], a_off[g1]) of the singles table, in batches of AB_NA
+// consecutive singles; a batch may span alpha rows.  The slabs of batch i+1
+// are copied (cp.async) while batch i is computed, and the entry sums are
+// flushed to sigma whenever the alpha row changes.
 
-__device__ __forceinline__ bool ab_next(const int64_t *__restrict__ a_off, int64_t g1,
-                                        ab_item &it) {
-    it.ab += AB_NA;
-    if (it.ab < it.a1) return true;
-    for (int64_t ia = it.ia + 1; ia < g1; ia++) {
-        int64_t a0 = a_off[ia], a1 = a_off[ia + 1];
-        if (a1 > a0) {
-            it.ia = ia;
-            it.ab = a0;
-            it.a1 = a1;
-            return true;
-        }
-    }
-    it.ia = g1;
-    return false;
-}
 
 // One (row, 256-column tile) of the same-spin product; blockDim.x == 256.
 template <bool DIAG>
@@ -113,6 +97,7 @@ __device__ __forceinline__ void alpha_beta_block(const ab_args &a, int64_t chunk
     double(*slab)[AB_NA][AB_YW] = reinterpret_cast<double(*)[AB_NA][AB_YW]>(ab_dyn);
     __shared__ int64_t sh_vrow[2][AB_NA];
     __shared__ uint32_t sh_sa[2][AB_NA];
+    __shared__ int64_t sh_row[2][AB_NA];
     __shared__ int64_t sh_off[AB_YW + 1];
 
     const int tid = threadIdx.x;
@@ -145,36 +130,45 @@ __device__ __forceinline__ void alpha_beta_block(const ab_args &a, int64_t chunk
     }
 
     const int64_t g0 = a.group_rows[group], g1 = a.group_rows[group + 1];
-    // stage the slabs and alpha data of one item into buffer `buf`
-    auto stage = [&](const ab_item &it, int buf) {
-        const int nbat = (int)min((int64_t)AB_NA, it.a1 - it.ab);
+    const int64_t xs = a.a_off[g0], xe = a.a_off[g1];
+    // stage the slabs and alpha data of the batch starting at single x0
+    auto stage = [&](int64_t x0, int buf) {
+        const int nbat = (int)min((int64_t)AB_NA, xe - x0);
         if (tid < nbat) {
-            sh_vrow[buf][tid] = (int64_t)a.a_pq[it.ab + tid] * a.norb2;
-            sh_sa[buf][tid] = (a.a_sgn[it.ab + tid] < 0) ? 1u : 0u;
+            const int64_t x = x0 + tid;
+            sh_vrow[buf][tid] = (int64_t)a.a_pq[x] * a.norb2;
+            sh_sa[buf][tid] = (a.a_sgn[x] < 0) ? 1u : 0u;
+            sh_row[buf][tid] = a.a_src[x];
         }
         for (int idx = tid; idx < nbat * width; idx += AB_THREADS) {
             int aa = idx / width, j = idx - aa * width;
-            cp_async8(&slab[buf][aa][j], a.C + (int64_t)a.a_tgt[it.ab + aa] * a.nb + y0 + j);
+            cp_async8(&slab[buf][aa][j], a.C + (int64_t)a.a_tgt[x0 + aa] * a.nb + y0 + j);
         }
         cp_async_commit();
     };
+    auto flush = [&](int64_t row) {
+#pragma unroll
+        for (int k = 0; k < AB_EPT; k++) {
+            if (ib[k] >= 0) atomicAdd(&a.S[row * a.nb + ib[k]], acc[k]);
+            acc[k] = 0.0;
+        }
+    };
 
-    ab_item cur;
-    cur.ia = g0 - 1;
-    cur.ab = 0;
-    cur.a1 = 0;
-    bool have = ab_next(a.a_off, g1, cur);
-    if (have) stage(cur, 0);
+    if (xs < xe) stage(xs, 0);
     int buf = 0;
-    while (have) {
-        ab_item nxt = cur;
-        bool more = ab_next(a.a_off, g1, nxt);
-        if (more) stage(nxt, buf ^ 1);
+    int64_t row_cur = -1;  // alpha row of the sums in acc (uniform across the block)
+    for (int64_t xb = xs; xb < xe; xb += AB_NA) {
+        if (xb + AB_NA < xe) stage(xb + AB_NA, buf ^ 1);
         else cp_async_commit();  // keep the group count uniform
         cp_async_wait<1>();
-        __syncthreads();  // slabs of `cur` visible to all threads
-        const int nbat = (int)min((int64_t)AB_NA, cur.a1 - cur.ab);
+        __syncthreads();  // slabs of this batch visible to all threads
+        const int nbat = (int)min((int64_t)AB_NA, xe - xb);
         for (int ai = 0; ai < nbat; ai++) {
+            const int64_t row = sh_row[buf][ai];
+            if (row != row_cur) {
+                if (row_cur >= 0) flush(row_cur);
+                row_cur = row;
+            }
             const double *vr = a.V + sh_vrow[buf][ai];
             const uint32_t sa = sh_sa[buf][ai] << 31;
             const double *sl = slab[buf][ai];
@@ -187,18 +181,10 @@ __device__ __forceinline__ void alpha_beta_block(const ab_args &a, int64_t chunk
                 acc[k] = fma(__longlong_as_double((long long)bits), sl[(inf >> 12) & 0x1ffu], acc[k]);
             }
         }
-        if (cur.ab + AB_NA >= cur.a1) {  // last batch of this alpha row: flush
-#pragma unroll
-            for (int k = 0; k < AB_EPT; k++) {
-                if (ib[k] >= 0) atomicAdd(&a.S[cur.ia * a.nb + ib[k]], acc[k]);
-                acc[k] = 0.0;
-            }
-        }
-        __syncthreads();  // buffer `buf` is reused by the item after next
-        cur = nxt;
-        have = more;
+        __syncthreads();  // buffer `buf` is reused by the batch after next
         buf ^= 1;
     }
+    if (row_cur >= 0) flush(row_cur);
     cp_async_wait<0>();
 }
 

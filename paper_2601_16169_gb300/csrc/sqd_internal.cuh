@@ -66,6 +66,7 @@ struct spin_tables {
     uint16_t *pq1 = nullptr;   // p*norb+q (p created, q annihilated)
     int8_t *sgn1 = nullptr;    // <J|a+_p a_q|I>
     double *val1 = nullptr;    // <I|H_s|J>
+    int32_t *src1 = nullptr;   // owning row of each entry (paired-singles batches)
 
     // doubles CSR
     int64_t nnz2 = 0;
@@ -219,8 +220,8 @@ int launch_block_dot(sqd_ctx *, const double *A, int64_t lda, int m, const doubl
                      int64_t ldx, int b, int64_t n, double *partial, int nblk, double *out,
                      int ldo);
 int launch_ritz_block(sqd_ctx *, const double *V, const double *W, int64_t ld, int m,
-                      const double *Y, const double *theta, int k, double *X, double *R,
-                      int64_t n, double *partial, int nblk, double *rnorm2);
+                      const double *Y, const double *theta, const int *sel, int ks, double *X,
+                      double *R, int64_t n, double *partial, int nblk, double *rnorm2);
 int launch_project_g(sqd_ctx *, double *G, int ldg, int m, const double *Z, int ldz, int r,
                      double *GZ);
 int launch_residual(sqd_ctx *, const double *X, const double *WY, const double *theta,

@@ -290,6 +290,24 @@ def test_davidson_guess_block_dependent(sqd, ctx):
     t.close()
 
 
+def test_davidson_outputs_consistent_when_stopped_early(sqd, ctx):
+    # stopped by max_iter: the returned vectors, energies and residual norms
+    # must still belong together (Ritz pairs of the final basis)
+    w = si.workload("h2o29", n_unique=70)
+    t = make_tables(sqd, ctx, w.norb, w.strings_a, 5, w.strings_b, 5, w.h, w.V)
+    H = oracle.dense_h(w.norb, w.h, w.V, 0.0, w.strings_a, w.strings_b)
+    for iters in (2, 7, 15):
+        e, X, it, res, rc = sqd.davidson(ctx, t, nroots=4, tol_residual=1e-12, tol_energy=1e-14,
+                                         max_iter=iters, raise_on_nonconvergence=False)
+        assert rc == sqd.SQD_ENOTCONVERGED and it == iters
+        Xh = X.cpu().numpy().reshape(4, -1)
+        assert np.allclose(Xh @ Xh.T, np.eye(4), atol=1e-10)
+        r = np.linalg.norm(Xh @ H - e[:, None] * Xh, axis=1)
+        assert np.allclose(r, res, rtol=1e-6, atol=1e-12)
+        assert np.allclose(np.einsum("ij,jk,ik->i", Xh, H, Xh), e, rtol=0, atol=1e-10)
+    t.close()
+
+
 def test_davidson_matches_oracle_davidson(sqd, ctx):
     # same algorithm on the oracle side (matrix-free oracle sigma)
     w = si.workload("h2o29", n_unique=120)
