@@ -243,6 +243,8 @@ def run_ours(args, rank, world, local_rank):
 
     for _ in range(args.warmup):
         step(raw_d, h_d, V_d)
+    # measured FP64 rates of this GPU (the derived peak is the roofline's)
+    fp64_dfma, fp64_dmma = ctx.measure_fp64_peaks()
     barrier()
     ctx.profile(True)
     clk = ClockSampler(local_rank)
@@ -318,6 +320,21 @@ def run_ours(args, rank, world, local_rank):
         "det_per_s": value * w.ndet,
         "sigma_fp64_tflops": sigma_flops / (sigma_ms / 1e3) / 1e12,
         "sigma_share_of_step": sigma_ms / dev_ms,
+        # whole-sigma bound: max(compulsory bytes / HBM, flops / FP64 peak)
+        "sigma_bound": {
+            "t_flops_ms": sigma_flops / (FP64_PEAK_TFLOPS * 1e12) * 1e3,
+            "t_bytes_ms": sum(prof[k]["bytes"] for k in ("same_spin_alpha", "same_spin_beta",
+                                                         "alpha_beta", "transpose"))
+            / (_hbm_peak() * 1e9) * 1e3,
+            "t_measured_ms": sigma_ms,
+            "frac": max(sigma_flops / (FP64_PEAK_TFLOPS * 1e12),
+                        sum(prof[k]["bytes"] for k in ("same_spin_alpha", "same_spin_beta",
+                                                       "alpha_beta", "transpose"))
+                        / (_hbm_peak() * 1e9)) / (sigma_ms / 1e3) if sigma_ms else None},
+        "tables_ms_per_step": (prof["tables"]["ms"] + prof["strings"]["ms"]) / args.steps,
+        "fp64_measured": {"dfma_tflops": fp64_dfma, "dmma_tflops": fp64_dmma,
+                          "note": "probe grids of independent FP64 FMA chains and of FP64 "
+                                  "tensor MMAs (m8n8k4) at the SM clock reported in clocks"},
         "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
         "roofline": roof,
         "hbm_roofline": {
@@ -474,7 +491,7 @@ def run_batched(args, rank, world, local_rank):
     ms_b = ev0.elapsed_time(ev1) / args.steps
     prof = ctx.profile_read()
     launches = ctx.launch_count()
-    scale = sqd.batched_tuning(ctx)
+    scale, device_loop = sqd.batched_tuning(ctx, with_loop=True)
     # the same work as one solve per subspace
     ctx.profile(False)
     torch.cuda.synchronize(dev)
@@ -501,6 +518,7 @@ def run_batched(args, rank, world, local_rank):
            "max_abs_energy_diff_vs_sequential": float(np.max(np.abs(np.asarray(e_b) - e_s))),
            "iterations_batched_max": int(np.max(it_b)), "iterations_sequential_max": int(max(it_s)),
            "autotuned_group_scale": scale, "det_total": float(np.sum(ndet)),
+           "loop_in_one_graph": device_loop,
            "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
            "clocks": clocks, "gpu_launches": launches}
     ctx.close()

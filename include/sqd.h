@@ -315,8 +315,11 @@ int sqd_davidson_batched(sqd_ctx *ctx, int nbatch, sqd_tables *const *tables,
                          const sqd_options *opt, double *h_energies, double *const *d_C,
                          int *h_iters, int *h_status);
 
-/* The alpha-group scale the last sqd_davidson_batched call chose (host). */
-int sqd_batched_tuning(const sqd_ctx *ctx, double *group_scale);
+/* What the last sqd_davidson_batched call chose (host outputs, each may be
+ * NULL): the alpha-group scale of the paired-singles split, and whether the
+ * iteration loop ran inside one graph (1: a conditional WHILE node decided on
+ * the device) or as host-driven replays of the captured iteration (0). */
+int sqd_batched_tuning(const sqd_ctx *ctx, double *group_scale, int *device_loop);
 
 /* ------------------------------------------------ adjoint: RDMs ----- */
 
@@ -367,6 +370,18 @@ int sqd_profile_enable(sqd_ctx *ctx, int enable);
 int sqd_profile_read(sqd_ctx *ctx, int cls, const char **name, int64_t *regions,
                      double *ms, double *flops, double *bytes);
 int sqd_launch_count(const sqd_ctx *ctx, int64_t *launches);
+
+/*
+ * FP64 throughput probes (not in the paper): the sigma and Davidson kernels
+ * are bound by FP64 arithmetic, so their roofline needs the FP64 rate of
+ * this GPU.  Runs a grid of independent FMA chains on the FP64 ALU pipe and
+ * a grid of FP64 tensor-core MMAs (m8n8k4), each as the best of three timed
+ * launches on the context stream after a warm-up, and returns TFLOP/s
+ * (2 flop per multiply-add) in the host doubles given (either may be NULL).
+ * Takes about a second; synchronises the stream.  Errors: SQD_EINVAL (NULL
+ * ctx), SQD_ECUDA.
+ */
+int sqd_measure_fp64_peaks(sqd_ctx *ctx, double *dfma_tflops, double *dmma_tflops);
 
 #ifdef __cplusplus
 }

@@ -49,7 +49,7 @@ EXPORTED = [
     "sqd_profile_enable", "sqd_profile_read", "sqd_launch_count", "sqd_orbital_gradient",
     "sqd_build_strings_noalloc", "sqd_davidson_batched", "sqd_batched_tuning",
     "sqd_stored_h_build", "sqd_sigma_stored", "sqd_string_weights", "sqd_select_strings",
-    "sqd_map_vector", "sqd_tables_set_sigma_mode",
+    "sqd_map_vector", "sqd_tables_set_sigma_mode", "sqd_measure_fp64_peaks",
 ]
 
 PROFILE_CLASSES = ["same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose", "tables",
@@ -112,7 +112,7 @@ def lib():
     L.sqd_orbital_gradient.argtypes = [vp, vp, vp, vp, vp]
     L.sqd_build_strings_noalloc.argtypes = [vp, vp, i64, i32, i32, vp, ctypes.POINTER(i64)]
     L.sqd_davidson_batched.argtypes = [vp, i32, vp, ctypes.POINTER(Options), vp, vp, vp, vp]
-    L.sqd_batched_tuning.argtypes = [vp, ctypes.POINTER(dbl)]
+    L.sqd_batched_tuning.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
     L.sqd_stored_h_build.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
     L.sqd_sigma_stored.argtypes = [vp, vp, vp, vp, i32]
     L.sqd_string_weights.argtypes = [vp, vp, vp, vp, vp]
@@ -120,6 +120,7 @@ def lib():
     L.sqd_map_vector.argtypes = [vp, vp, i64, vp, i64, vp, vp, i64, vp, i64, vp,
                                  ctypes.POINTER(dbl)]
     L.sqd_tables_set_sigma_mode.argtypes = [vp, i32]
+    L.sqd_measure_fp64_peaks.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     _LIB = L
     return L
 
@@ -189,6 +190,12 @@ class Context:
         n = ctypes.c_int64()
         self._check(self._lib.sqd_launch_count(self.handle, ctypes.byref(n)))
         return n.value
+
+    def measure_fp64_peaks(self):
+        """sqd_measure_fp64_peaks: (FP64 FMA pipe, FP64 tensor MMA) TFLOP/s."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.sqd_measure_fp64_peaks(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def close(self):
         if getattr(self, "handle", None):
@@ -436,11 +443,13 @@ def map_vector(ctx: Context, old_a: torch.Tensor, old_b: torch.Tensor, C: torch.
     return out, nrm.value
 
 
-def batched_tuning(ctx: Context) -> float:
-    """sqd_batched_tuning: alpha-group scale chosen by the last batched solve."""
+def batched_tuning(ctx: Context, with_loop: bool = False):
+    """sqd_batched_tuning: alpha-group scale chosen by the last batched solve
+    (and, with_loop=True, whether its iteration loop ran inside one graph)."""
     v = ctypes.c_double()
-    ctx._check(ctx._lib.sqd_batched_tuning(ctx.handle, ctypes.byref(v)))
-    return v.value
+    dl = ctypes.c_int()
+    ctx._check(ctx._lib.sqd_batched_tuning(ctx.handle, ctypes.byref(v), ctypes.byref(dl)))
+    return (v.value, bool(dl.value)) if with_loop else v.value
 
 
 def rdm(ctx: Context, tables: Tables, C: torch.Tensor, two_body: bool = True):

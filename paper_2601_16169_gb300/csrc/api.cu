@@ -182,6 +182,12 @@ int sqd_launch_count(const sqd_ctx *ctx, int64_t *launches) {
     return SQD_OK;
 }
 
+int sqd_measure_fp64_peaks(sqd_ctx *ctx, double *dfma_tflops, double *dmma_tflops) {
+    if (!ctx) return fail_noctx(SQD_EINVAL, "sqd_measure_fp64_peaks: ctx is NULL");
+    SQD_TRY(use_device(ctx));
+    return measure_fp64_peaks(ctx, dfma_tflops, dmma_tflops);
+}
+
 const char *sqd_last_error(const sqd_ctx *ctx) {
     return ctx ? ctx->err.c_str() : g_err.c_str();
 }
@@ -414,7 +420,7 @@ void sqd_free_tables(sqd_tables *t) {
     cudaDeviceSynchronize();
     free_spin(&t->a);
     if (!t->shared) free_spin(&t->b_own);
-    void *ptrs[] = {t->h,         t->V,          t->diag,       t->ab.chunk_rows,
+    void *ptrs[] = {t->h,         t->V,          t->diag,       t->ab.chunk_e, t->ab.chunk_y,
                     t->ab.group_rows, t->scratch_t, t->scratch_s, t->rdm_iket,
                     t->rdm_ibra,  t->rdm_ipq,    t->rdm_chunks, t->rdm_groups,
                     t->st_rowptr, t->st_col,     t->st_val,  t->Vf,
@@ -950,9 +956,10 @@ int sqd_davidson_batched(sqd_ctx *ctx, int nbatch, sqd_tables *const *tables,
     return davidson_batched_impl(ctx, nbatch, tables, o, h_energies, d_C, h_iters, h_status);
 }
 
-int sqd_batched_tuning(const sqd_ctx *ctx, double *group_scale) {
-    if (!ctx || !group_scale) return fail_noctx(SQD_EINVAL, "sqd_batched_tuning: NULL argument");
-    *group_scale = ctx->batched_group_scale;
+int sqd_batched_tuning(const sqd_ctx *ctx, double *group_scale, int *device_loop) {
+    if (!ctx) return fail_noctx(SQD_EINVAL, "sqd_batched_tuning: NULL argument");
+    if (group_scale) *group_scale = ctx->batched_group_scale;
+    if (device_loop) *device_loop = ctx->batched_device_loop;
     return SQD_OK;
 }
 

@@ -40,6 +40,7 @@ __device__ __forceinline__ void jacobi_block(const double *__restrict__ G, int l
     extern __shared__ double jac_sh[];
     __shared__ double cs[JAC_MAX / 2], sn[JAC_MAX / 2];
     __shared__ int pp[JAC_MAX / 2], qq[JAC_MAX / 2];
+    __shared__ int act[JAC_MAX / 2], wcnt[2];
     __shared__ double red[32];
     __shared__ int done;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -99,21 +100,41 @@ __device__ __forceinline__ void jacobi_block(const double *__restrict__ G, int l
                 double apq = A(p, q);
                 double c = 1.0, s = 0.0;
                 if (apq != 0.0) {
-                    double tau = (A(q, q) - A(p, p)) / (2.0 * apq);
-                    double t = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau))
-                                            : -1.0 / (-tau + sqrt(1.0 + tau * tau));
-                    c = 1.0 / sqrt(1.0 + t * t);
-                    s = t * c;
+                    if (fabs(apq) <= 0x1p-60 * fmin(fabs(A(p, p)), fabs(A(q, q)))) {
+                        // negligible against both diagonal entries: set to zero
+                        // (no other pair of this step touches entry (p, q))
+                        A(p, q) = 0.0;
+                        A(q, p) = 0.0;
+                    } else {
+                        double tau = (A(q, q) - A(p, p)) / (2.0 * apq);
+                        double t = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau))
+                                                : -1.0 / (-tau + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        s = t * c;
+                    }
                 }
                 pp[tid] = p;
                 qq[tid] = q;
                 cs[tid] = c;
                 sn[tid] = s;
             }
+            // compact the pairs that rotate (s != 0): the updates below cost
+            // FP64 issue per warp instruction, so identity rotations are dropped
+            bool on = false;
+            unsigned bal = 0u;
+            if (tid < 64) {
+                on = (tid < npair) && (sn[tid] != 0.0);
+                bal = __ballot_sync(0xffffffffu, on);
+                if ((tid & 31) == 0) wcnt[tid >> 5] = __popc(bal);
+            }
             __syncthreads();
+            if (on) act[__popc(bal & ((1u << (tid & 31)) - 1u)) + ((tid >> 5) ? wcnt[0] : 0)] = tid;
+            const int nact = wcnt[0] + wcnt[1];
+            __syncthreads();
+            if (nact == 0) continue;  // uniform across the block
             // columns: A <- A J, Q <- Q J
-            for (int t = tid; t < M * npair; t += nt) {
-                int r = t / npair, k = t % npair;
+            for (int t = tid; t < M * nact; t += nt) {
+                int r = t / nact, k = act[t % nact];
                 int p = pp[k], q = qq[k];
                 double c = cs[k], s = sn[k];
                 double ap = A(r, p), aq = A(r, q);
@@ -125,8 +146,8 @@ __device__ __forceinline__ void jacobi_block(const double *__restrict__ G, int l
             }
             __syncthreads();
             // rows: A <- J^T A
-            for (int t = tid; t < M * npair; t += nt) {
-                int col = t / npair, k = t % npair;
+            for (int t = tid; t < M * nact; t += nt) {
+                int col = t / nact, k = act[t % nact];
                 int p = pp[k], q = qq[k];
                 double c = cs[k], s = sn[k];
                 double ap = A(p, col), aq = A(q, col);

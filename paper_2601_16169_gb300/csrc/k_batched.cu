@@ -452,6 +452,14 @@ __global__ void __launch_bounds__(256) kb_jacobi(const bdesc *__restrict__ D,
     jacobi_block(d.G, M, S[b].m, d.evals, d.evecs);
 }
 
+// end of a loop iteration on the device: run the body again while some
+// subspace is active and the iteration limit is not reached
+__global__ void kb_loop_control(const int *__restrict__ active, int *__restrict__ iters,
+                                int limit, cudaGraphConditionalHandle h) {
+    const int it = ++(*iters);
+    cudaGraphSetConditional(h, (*active > 0 && it < limit) ? 1u : 0u);
+}
+
 __global__ void kb_count_active(const bstate *__restrict__ S, int nprob, int *out) {
     __shared__ int c;
     if (threadIdx.x == 0) c = 0;
@@ -562,11 +570,17 @@ static std::vector<int64_t> alpha_groups(const spin_tables *A, int64_t ng) {
     return g;
 }
 
-// launch the three sigma stages for every subspace flagged newvec
+__global__ void kb_zero_counters(unsigned long long *c, int n) {
+    if ((int)threadIdx.x < n) c[threadIdx.x] = 0ull;
+}
+
+// launch the three sigma stages for every subspace flagged newvec (kernels
+// only, so the sequence can be the body of a conditional graph node)
 static int launch_sigma_stages(sqd_ctx *ctx, batched_plan &p) {
     const int n = p.nprob;
     const int sm = ctx->sm_count;
-    SQD_CUDA(ctx, cudaMemsetAsync(p.counters, 0, sizeof(unsigned long long) * 5, ctx->stream));
+    kb_zero_counters<<<1, 32, 0, ctx->stream>>>(p.counters, 5);
+    SQD_LAUNCHED(ctx);
     kb_same_spin<true><<<8 * sm, 256, 0, ctx->stream>>>(p.D, p.S, p.pre_ssa, n, p.counters + 0);
     SQD_LAUNCHED(ctx);
     kb_transpose<0><<<8 * sm, dim3(32, 8), 0, ctx->stream>>>(p.D, p.S, p.pre_t0, n,
@@ -784,7 +798,12 @@ int davidson_batched_impl(sqd_ctx *ctx, int nprob, sqd_tables *const *tables,
     P.floor_ = o->precond_floor;
     P.max_iter = o->max_iter;
 
-    // --- capture one iteration, replay until no subspace is active ---------
+    // --- the iteration loop as one graph -------------------------------------
+    // The iteration is captured once as the body of a conditional WHILE node
+    // whose last kernel decides on the device whether to run it again, so
+    // the whole solve is one graph launch with no host round trip.  Where
+    // conditional nodes are unavailable, the captured iteration is replayed
+    // from the host instead, reading the active count after each replay.
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;
@@ -793,30 +812,87 @@ int davidson_batched_impl(sqd_ctx *ctx, int nprob, sqd_tables *const *tables,
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess)
         return fail(sqd_fail(ctx, SQD_ECUDA, "setup failed: %s",
                              cudaGetErrorString(cudaGetLastError())));
+    const int limit = o->max_iter + 2;
+    int *d_iters = nullptr;
+    if ((rc = plan_alloc(ctx, p, (void **)&d_iters, sizeof(int))) != SQD_OK) return fail(rc);
     cudaStream_t user = ctx->stream;
-    ctx->stream = cap;
     int64_t before = ctx->launches;
-    bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-    int irc = ok ? launch_iteration(ctx, p, P) : SQD_ECUDA;
-    ok = (cudaStreamEndCapture(cap, &graph) == cudaSuccess) && ok && irc == SQD_OK;
+    bool device_loop = false;
+    int irc = SQD_OK;
+    {
+        cudaGraphConditionalHandle h;
+        cudaGraphNodeParams cp = {};
+        cudaGraphNode_t cnode;
+        bool ok = cudaMemsetAsync(d_iters, 0, sizeof(int), user) == cudaSuccess &&
+                  cudaStreamSynchronize(user) == cudaSuccess &&
+                  cudaGraphCreate(&graph, 0) == cudaSuccess &&
+                  cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) ==
+                      cudaSuccess;
+        if (ok) {
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            ok = cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp) == cudaSuccess;
+        }
+        if (ok) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            ctx->stream = cap;
+            ok = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                irc = launch_iteration(ctx, p, P);
+                kb_loop_control<<<1, 1, 0, cap>>>(p.d_active, d_iters, limit, h);
+                ok = (cudaStreamEndCapture(cap, &body) == cudaSuccess) && irc == SQD_OK;
+            }
+            ctx->stream = user;
+        }
+        if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        if (ok) {
+            device_loop = true;
+        } else {
+            if (graph) cudaGraphDestroy(graph);
+            graph = nullptr;
+            exec = nullptr;
+            cudaGetLastError();
+        }
+    }
     const int64_t per_iter = ctx->launches - before;
     ctx->launches = before;
-    ctx->stream = user;
-    if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
-    if (!ok) {
-        if (graph) cudaGraphDestroy(graph);
-        cudaStreamDestroy(cap);
-        cudaGetLastError();
-        return fail(sqd_fail(ctx, SQD_ECUDA, "graph capture of the batched iteration failed"));
+    if (!device_loop) {
+        // fallback: one captured iteration replayed from the host
+        ctx->stream = cap;
+        bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        irc = ok ? launch_iteration(ctx, p, P) : SQD_ECUDA;
+        ok = (cudaStreamEndCapture(cap, &graph) == cudaSuccess) && ok && irc == SQD_OK;
+        ctx->launches = before;
+        ctx->stream = user;
+        if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        if (!ok) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaStreamDestroy(cap);
+            cudaGetLastError();
+            return fail(sqd_fail(ctx, SQD_ECUDA, "graph capture of the batched iteration failed"));
+        }
     }
-    int active = nprob, iters = 0;
-    while (active > 0 && iters <= o->max_iter + 1) {
-        if (cudaGraphLaunch(exec, ctx->stream) != cudaSuccess) break;
-        ctx->launches += per_iter;
-        cudaMemcpyAsync(&active, p.d_active, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
-        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) break;
-        iters++;
+    int iters = 0;
+    if (device_loop) {
+        if (cudaGraphLaunch(exec, ctx->stream) == cudaSuccess &&
+            cudaMemcpyAsync(&iters, d_iters, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) ==
+                cudaSuccess)
+            cudaStreamSynchronize(ctx->stream);
+        ctx->launches += per_iter * iters;
+    } else {
+        int active = nprob;
+        while (active > 0 && iters < limit) {
+            if (cudaGraphLaunch(exec, ctx->stream) != cudaSuccess) break;
+            ctx->launches += per_iter;
+            cudaMemcpyAsync(&active, p.d_active, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+            if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) break;
+            iters++;
+        }
     }
+    ctx->batched_device_loop = device_loop ? 1 : 0;
     cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
     cudaStreamDestroy(cap);

@@ -98,7 +98,8 @@ ab_args make_ab_args(const sqd_tables *t, const double *C, double *S) {
     a.b_tgt = B->tgt1;
     a.b_pq = B->pq1;
     a.b_sgn = B->sgn1;
-    a.chunk_rows = t->ab.chunk_rows;
+    a.chunk_e = t->ab.chunk_e;
+    a.chunk_y = t->ab.chunk_y;
     a.group_rows = t->ab.group_rows;
     a.C = C;
     a.S = S;
@@ -124,7 +125,8 @@ int launch_alpha_beta(sqd_ctx *ctx, const sqd_tables *t, const double *C, double
 int set_ab_groups(sqd_ctx *ctx, sqd_tables *t, double scale) {
     const spin_tables *A = &t->a;
     const int64_t target_blocks = (int64_t)(scale * 16.0 * ctx->sm_count + 0.5);
-    int64_t G = (target_blocks + t->ab.nchunks - 1) / t->ab.nchunks;
+    const int64_t nch = std::max(1, t->ab.nchunks);
+    int64_t G = (target_blocks + nch - 1) / nch;
     if (G > A->n) G = A->n;
     if (G < 1) G = 1;
     if (G > 65535) G = 65535;
@@ -171,21 +173,32 @@ int build_ab_schedule(sqd_ctx *ctx, sqd_tables *t) {
             SQD_LAUNCHED(ctx);
         }
     }
-    std::vector<int64_t> chunks{0};
+    // beta chunks: AB_ECAP consecutive single entries (a row may be split
+    // between chunks), cut earlier where they would span more than AB_YW rows
     const std::vector<int64_t> &bo = B->h_off1;
-    int64_t y = 0;
-    while (y < B->n) {
-        int64_t y_end = y;
-        while (y_end < B->n && y_end - y < AB_YW && bo[y_end + 1] - bo[y] <= AB_ECAP) y_end++;
-        if (y_end == y) y_end = y + 1;  // cannot happen: a row has <= 1024 singles
-        chunks.push_back(y_end);
-        y = y_end;
+    const int64_t nb = B->n, nnz = bo[nb];
+    std::vector<int64_t> ce{0}, cy;
+    int64_t e = 0, r = 0;
+    while (e < nnz) {
+        while (bo[r + 1] <= e) r++;  // row of entry e
+        int64_t end = std::min<int64_t>(e + AB_ECAP, nnz);
+        if (r + AB_YW < nb && bo[r + AB_YW] < end) end = bo[r + AB_YW];
+        int64_t r2 = r;
+        while (bo[r2 + 1] < end) r2++;  // row of entry end-1
+        cy.push_back(r);
+        cy.push_back(r2 + 1);
+        ce.push_back(end);
+        e = end;
     }
-    t->ab.nchunks = (int)chunks.size() - 1;
-    SQD_CUDA(ctx, cudaMalloc((void **)&t->ab.chunk_rows, sizeof(int64_t) * chunks.size()));
-    SQD_CUDA(ctx, cudaMemcpy(t->ab.chunk_rows, chunks.data(), sizeof(int64_t) * chunks.size(),
+    t->ab.nchunks = (int)cy.size() / 2;
+    SQD_CUDA(ctx, cudaMalloc((void **)&t->ab.chunk_e, sizeof(int64_t) * ce.size()));
+    SQD_CUDA(ctx, cudaMalloc((void **)&t->ab.chunk_y, sizeof(int64_t) * (cy.size() + 2)));
+    SQD_CUDA(ctx, cudaMemcpy(t->ab.chunk_e, ce.data(), sizeof(int64_t) * ce.size(),
                              cudaMemcpyHostToDevice));
-    t->bytes += sizeof(int64_t) * chunks.size();
+    if (!cy.empty())
+        SQD_CUDA(ctx, cudaMemcpy(t->ab.chunk_y, cy.data(), sizeof(int64_t) * cy.size(),
+                                 cudaMemcpyHostToDevice));
+    t->bytes += sizeof(int64_t) * (ce.size() + cy.size() + 2);
     return set_ab_groups(ctx, t, 1.0);
 }
 

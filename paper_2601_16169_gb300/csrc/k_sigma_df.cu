@@ -119,8 +119,9 @@ __global__ void __launch_bounds__(AB_THREADS, 2)
                     const int32_t *__restrict__ a_src, const int32_t *__restrict__ a_tgt, const uint16_t *__restrict__ a_pq,
                     const int8_t *__restrict__ a_sgn, const int64_t *__restrict__ b_off,
                     const int32_t *__restrict__ b_tgt, const uint16_t *__restrict__ b_pq,
-                    const int8_t *__restrict__ b_sgn, const int64_t *__restrict__ chunk_rows,
-                    const int64_t *__restrict__ group_rows, const float2 *__restrict__ C,
+                    const int8_t *__restrict__ b_sgn, const int64_t *__restrict__ chunk_e,
+                    const int64_t *__restrict__ chunk_y, const int64_t *__restrict__ group_rows,
+                    const float2 *__restrict__ C,
                     double *__restrict__ S, const float2 *__restrict__ V) {
     extern __shared__ float2 abdf_dyn[];
     float2(*slab)[AB_NA][AB_YW] = reinterpret_cast<float2(*)[AB_NA][AB_YW]>(abdf_dyn);
@@ -130,11 +131,12 @@ __global__ void __launch_bounds__(AB_THREADS, 2)
     __shared__ int64_t sh_off[AB_YW + 1];
 
     const int tid = threadIdx.x;
-    const int64_t y0 = chunk_rows[blockIdx.x], y1 = chunk_rows[blockIdx.x + 1];
+    const int64_t e0 = chunk_e[blockIdx.x], e1 = chunk_e[blockIdx.x + 1];
+    const int64_t y0 = chunk_y[2 * blockIdx.x], y1 = chunk_y[2 * blockIdx.x + 1];
     const int width = (int)(y1 - y0);
     for (int t = tid; t <= width; t += AB_THREADS) sh_off[t] = b_off[y0 + t];
     __syncthreads();
-    const int64_t e0 = sh_off[0], e1 = sh_off[width];
+    const int nk = (int)((e1 - e0 + AB_THREADS - 1) / AB_THREADS);  // entry slots in use
 
     int32_t ib[AB_EPT];
     uint32_t info[AB_EPT];
@@ -191,23 +193,28 @@ __global__ void __launch_bounds__(AB_THREADS, 2)
         cp_async_wait<1>();
         __syncthreads();
         const int nbat = (int)min((int64_t)AB_NA, xe - xb);
-        for (int ai = 0; ai < nbat; ai++) {
-            const int64_t row = sh_row[buf][ai];
-            if (row != row_cur) {
-                if (row_cur >= 0) flush(row_cur);
-                row_cur = row;
-            }
-            const float2 *vr = V + sh_vrow[buf][ai];
-            const uint32_t sa = sh_sa[buf][ai] << 31;
-            const float2 *sl = slab[buf][ai];
+        auto pairs = [&](auto km) {
+            constexpr int KM = decltype(km)::value;
+            for (int ai = 0; ai < nbat; ai++) {
+                const int64_t row = sh_row[buf][ai];
+                if (row != row_cur) {
+                    if (row_cur >= 0) flush(row_cur);
+                    row_cur = row;
+                }
+                const float2 *vr = V + sh_vrow[buf][ai];
+                const uint32_t sa = sh_sa[buf][ai] << 31;
+                const float2 *sl = slab[buf][ai];
 #pragma unroll
-            for (int k = 0; k < AB_EPT; k++) {
-                const uint32_t inf = info[k];
-                const float2 v = df_neg_if(__ldg(vr + (inf & 0xfffu)), ((inf ^ sa) & 0x80000000u) != 0);
-                const float2 c = sl[(inf >> 12) & 0x1ffu];
-                df_mac(v.x, v.y, c.x, c.y, as[k], ae[k]);
+                for (int k = 0; k < KM; k++) {
+                    const uint32_t inf = info[k];
+                    const float2 v =
+                        df_neg_if(__ldg(vr + (inf & 0xfffu)), ((inf ^ sa) & 0x80000000u) != 0);
+                    const float2 c = sl[(inf >> 12) & 0x1ffu];
+                    df_mac(v.x, v.y, c.x, c.y, as[k], ae[k]);
+                }
             }
-        }
+        };
+        AB_DISPATCH(nk, pairs);
         __syncthreads();
         buf ^= 1;
     }
@@ -276,8 +283,8 @@ static int launch_alpha_beta_df(sqd_ctx *ctx, sqd_tables *t, const void *Cv, dou
     k_alpha_beta_df<<<dim3((unsigned)t->ab.nchunks, (unsigned)t->ab.ngroups), AB_THREADS, shm,
                       ctx->stream>>>(B->n, t->norb * t->norb, A->off1, A->src1, A->tgt1, A->pq1,
                                      A->sgn1,
-                                     B->off1, B->tgt1, B->pq1, B->sgn1, t->ab.chunk_rows,
-                                     t->ab.group_rows, (const float2 *)Cv, S, t->Vf);
+                                     B->off1, B->tgt1, B->pq1, B->sgn1, t->ab.chunk_e,
+                                     t->ab.chunk_y, t->ab.group_rows, (const float2 *)Cv, S, t->Vf);
     SQD_LAUNCHED(ctx);
     return SQD_OK;
 }

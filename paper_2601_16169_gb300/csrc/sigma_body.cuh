@@ -34,7 +34,8 @@ struct ab_args {
     const int32_t *b_tgt;
     const uint16_t *b_pq;
     const int8_t *b_sgn;
-    const int64_t *chunk_rows;
+    const int64_t *chunk_e;  // entry range [chunk_e[c], chunk_e[c+1]) of beta chunk c
+    const int64_t *chunk_y;  // its beta rows [chunk_y[2c], chunk_y[2c+1])
     const int64_t *group_rows;
     const double *C;
     double *S;
@@ -45,11 +46,38 @@ ss_args make_ss_args(const spin_tables *R, const spin_tables *Cc, int64_t nrows,
                      const double *C, double *S, const double *diag);
 ab_args make_ab_args(const sqd_tables *t, const double *C, double *S);
 
+// compile-time integer for templated lambdas
+template <int N>
+struct ab_int {
+    static constexpr int value = N;
+};
+// call f(ab_int<n>{}) for n in [1, 16] (uniform across the block)
+#define AB_DISPATCH(n, f)                  \
+    switch (n) {                           \
+        case 1: f(ab_int<1>{}); break;     \
+        case 2: f(ab_int<2>{}); break;     \
+        case 3: f(ab_int<3>{}); break;     \
+        case 4: f(ab_int<4>{}); break;     \
+        case 5: f(ab_int<5>{}); break;     \
+        case 6: f(ab_int<6>{}); break;     \
+        case 7: f(ab_int<7>{}); break;     \
+        case 8: f(ab_int<8>{}); break;     \
+        case 9: f(ab_int<9>{}); break;     \
+        case 10: f(ab_int<10>{}); break;   \
+        case 11: f(ab_int<11>{}); break;   \
+        case 12: f(ab_int<12>{}); break;   \
+        case 13: f(ab_int<13>{}); break;   \
+        case 14: f(ab_int<14>{}); break;   \
+        case 15: f(ab_int<15>{}); break;   \
+        default: f(ab_int<16>{}); break;   \
+    }
+
 #define AB_THREADS 256
 #define AB_EPT 16                          // beta entries per thread
 #define AB_ECAP (AB_THREADS * AB_EPT)      // beta entries per block
 #define AB_YW 256                          // beta rows (slab width) per block
 #define AB_NA 16                           // alpha singles staged per batch
+static_assert(AB_EPT == 16, "AB_DISPATCH covers 1..16 entry slots");
 
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -80,7 +108,10 @@ __device__ __forceinline__ void same_spin_tile(const ss_args &a, int64_t row, in
         int64_t J = a.tgt1[e];
         double c = C[J * ncols + col];
         double w = a.W[(int64_t)a.pq1[e] * ncols + col];
-        w = (a.sgn1[e] < 0) ? -w : w;
+        // sign of the coupling as an integer flip of the sign bit: a
+        // negation would cost an FP64 add, the pipe every term is bound by
+        w = __longlong_as_double(__double_as_longlong(w) ^
+                                 ((long long)(a.sgn1[e] < 0) << 63));
         acc = fma(a.val1[e], c, acc);
         acc = fma(w, c, acc);
     }
@@ -101,11 +132,14 @@ __device__ __forceinline__ void alpha_beta_block(const ab_args &a, int64_t chunk
     __shared__ int64_t sh_off[AB_YW + 1];
 
     const int tid = threadIdx.x;
-    const int64_t y0 = a.chunk_rows[chunk], y1 = a.chunk_rows[chunk + 1];
+    const int64_t e0 = a.chunk_e[chunk], e1 = a.chunk_e[chunk + 1];
+    const int64_t y0 = a.chunk_y[2 * chunk], y1 = a.chunk_y[2 * chunk + 1];
     const int width = (int)(y1 - y0);
     for (int t = tid; t <= width; t += AB_THREADS) sh_off[t] = a.b_off[y0 + t];
     __syncthreads();
-    const int64_t e0 = sh_off[0], e1 = sh_off[width];
+    // entry slots in use: the pair loop runs over these only (a predicated-off
+    // FP64 instruction still takes its issue slot)
+    const int nk = (int)((e1 - e0 + AB_THREADS - 1) / AB_THREADS);
 
     // this thread's beta entries: neighbour Ib and packed
     // (V column | slab column << 12 | sign << 31)
@@ -163,24 +197,28 @@ __device__ __forceinline__ void alpha_beta_block(const ab_args &a, int64_t chunk
         cp_async_wait<1>();
         __syncthreads();  // slabs of this batch visible to all threads
         const int nbat = (int)min((int64_t)AB_NA, xe - xb);
-        for (int ai = 0; ai < nbat; ai++) {
-            const int64_t row = sh_row[buf][ai];
-            if (row != row_cur) {
-                if (row_cur >= 0) flush(row_cur);
-                row_cur = row;
-            }
-            const double *vr = a.V + sh_vrow[buf][ai];
-            const uint32_t sa = sh_sa[buf][ai] << 31;
-            const double *sl = slab[buf][ai];
+        auto pairs = [&](auto km) {
+            constexpr int KM = decltype(km)::value;
+            for (int ai = 0; ai < nbat; ai++) {
+                const int64_t row = sh_row[buf][ai];
+                if (row != row_cur) {
+                    if (row_cur >= 0) flush(row_cur);
+                    row_cur = row;
+                }
+                const double *vr = a.V + sh_vrow[buf][ai];
+                const uint32_t sa = sh_sa[buf][ai] << 31;
+                const double *sl = slab[buf][ai];
 #pragma unroll
-            for (int k = 0; k < AB_EPT; k++) {
-                const uint32_t inf = info[k];
-                double v = __ldg(vr + (inf & 0xfffu));
-                unsigned long long bits = (unsigned long long)__double_as_longlong(v) ^
-                                          ((unsigned long long)((inf ^ sa) & 0x80000000u) << 32);
-                acc[k] = fma(__longlong_as_double((long long)bits), sl[(inf >> 12) & 0x1ffu], acc[k]);
+                for (int k = 0; k < KM; k++) {
+                    const uint32_t inf = info[k];
+                    double v = __ldg(vr + (inf & 0xfffu));
+                    unsigned long long bits = (unsigned long long)__double_as_longlong(v) ^
+                                              ((unsigned long long)((inf ^ sa) & 0x80000000u) << 32);
+                    acc[k] = fma(__longlong_as_double((long long)bits), sl[(inf >> 12) & 0x1ffu], acc[k]);
+                }
             }
-        }
+        };
+        AB_DISPATCH(nk, pairs);
         __syncthreads();  // buffer `buf` is reused by the batch after next
         buf ^= 1;
     }

@@ -46,6 +46,7 @@ struct sqd_ctx {
     double cls_bytes[PROF_NCLASS] = {0};
     double cls_ms[PROF_NCLASS] = {0};
     double batched_group_scale = 0.0;    // last autotuned alpha-group scale
+    int batched_device_loop = 0;         // 1: last batched solve looped inside one graph
 };
 
 // Time the launches between prof_begin/prof_end as one region of class cls
@@ -91,7 +92,8 @@ struct spin_tables {
 struct ab_schedule {
     // beta chunks: rows [rows[c], rows[c+1]) of the beta singles table
     int nchunks = 0;
-    int64_t *chunk_rows = nullptr;  // device, nchunks+1
+    int64_t *chunk_e = nullptr;  // device, nchunks+1: entry ranges of the beta singles
+    int64_t *chunk_y = nullptr;  // device, 2*nchunks: [first, end) beta rows of each chunk
     // alpha row groups: [grp[g], grp[g+1])
     int ngroups = 0;
     int64_t *group_rows = nullptr;  // device, ngroups+1
@@ -199,6 +201,7 @@ int launch_same_spin(sqd_ctx *, const spin_tables *rows, const spin_tables *cols
                      int64_t nrows, int64_t ncols, const double *C, double *S,
                      const double *diag);
 int launch_alpha_beta(sqd_ctx *, const sqd_tables *t, const double *C, double *S);
+int measure_fp64_peaks(sqd_ctx *, double *dfma_tflops, double *dmma_tflops);
 int set_ab_groups(sqd_ctx *, sqd_tables *t, double scale);
 int tune_ab_groups(sqd_ctx *, sqd_tables *t, int mode,
                    int (*launch)(sqd_ctx *, sqd_tables *, const void *, double *), const void *C);

@@ -36,7 +36,9 @@ def _compare(sqd, ctx, subs, tol_r=1e-8):
     tabs = [_tables(sqd, ctx, w) for w in subs]
     e, Cs, it, st, rc = sqd.davidson_batched(ctx, tabs, tol_residual=tol_r, tol_energy=1e-10)
     assert rc == 0 and np.all(st == 0)
-    assert 0.0 < sqd.batched_tuning(ctx) <= 1.0
+    scale, device_loop = sqd.batched_tuning(ctx, with_loop=True)
+    assert 0.0 < scale <= 1.0
+    assert device_loop  # the iteration loop ran inside one graph
     for b, t in enumerate(tabs):
         e1, X1, _, _, _ = sqd.davidson(ctx, t, nroots=1, tol_residual=tol_r, tol_energy=1e-10)
         assert abs(e[b] - e1[0]) <= 1e-9, (b, e[b], e1[0])
