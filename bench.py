@@ -81,6 +81,8 @@ def _args():
     p.add_argument("--nbatch", type=int, default=64)
     p.add_argument("--sigma-mode", type=int, default=0, choices=[0, 1],
                    help="0: native FP64 sigma (headline); 1: double-float on the FP32 pipe")
+    p.add_argument("--correction", default="davidson", choices=["davidson", "olsen"],
+                   help="Davidson correction vector (olsen: orthogonal to the Ritz vector)")
     p.add_argument("--max-subspace", type=int, default=None,
                    help="Davidson subspace limit (default max(8 nroots, 16))")
     p.add_argument("--stored", action="store_true",
@@ -217,6 +219,8 @@ def run_ours(args, rank, world, local_rank):
     opts = dict(SOLVE[args.workload])
     if args.max_subspace:
         opts["max_subspace"] = args.max_subspace
+    if args.correction != "davidson":
+        opts["correction"] = args.correction
     ctx = sqd.Context(local_rank)
     stream = torch.cuda.current_stream(dev)
 

@@ -263,6 +263,8 @@ typedef struct {
     double precond_floor;/* clamp of |theta - H_II| (e.g. 1e-8)                */
     int use_guess;       /* 1: d_C holds nroots initial vectors                */
     int use_stored_h;    /* 1: apply the stored matrix (sqd_stored_h_build)    */
+    int correction;      /* 0: Davidson t = r/(theta - H_II); 1: Olsen's       */
+                         /*    t = (r - eps x)/(theta - H_II) with x^T t = 0   */
 } sqd_options;
 
 /*
@@ -272,7 +274,10 @@ typedef struct {
  *
  * Guess: unit vectors on the nroots smallest H_II (ties: lower index), or
  * the nroots vectors in d_C if use_guess.  Correction t = r / (theta -
- * H_II) with |denominator| clamped to precond_floor; classical Gram-Schmidt
+ * H_II) with |denominator| clamped to precond_floor (correction = 1: Olsen's
+ * modification, t = (r - eps x) / (theta - H_II) with eps chosen so that
+ * x^T t = 0, J. Olsen, P. Jorgensen, J. Simons, Chem. Phys. Lett. 169, 463
+ * (1990); not in the paper, off by default); classical Gram-Schmidt
  * twice, a vector is dropped if its norm after that is below 1e-12; at the
  * subspace limit the basis restarts from the 2*nroots lowest Ritz vectors
  * plus the nroots Ritz vectors of the previous iteration orthonormalised

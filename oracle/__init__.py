@@ -324,9 +324,26 @@ def _fix_phase(X):
     return X
 
 
+def correction_vector(r, x, theta, hdiag, precond_floor=1e-8, correction="davidson"):
+    """The Davidson correction of one root: t = r / D with D = theta - H_II
+    clamped to sign * max(|D|, precond_floor) (sign + for D = 0); with
+    correction="olsen", t = (r - eps x) / D, eps = (x^T D^-1 r) / (x^T D^-1 x),
+    which makes x^T t = 0 (Olsen, Jorgensen, Simons 1990; not in the paper)."""
+    den = theta - hdiag
+    den = np.where(np.abs(den) < precond_floor,
+                   np.where(den < 0, -precond_floor, precond_floor), den)
+    if correction == "olsen":
+        b = x @ (x / den)
+        eps = (x @ (r / den)) / b if b != 0.0 else 0.0
+        r = r - eps * x
+    elif correction != "davidson":
+        raise ValueError(correction)
+    return r / den
+
+
 def davidson(matvec, hdiag, nroots=1, tol_residual=1e-8, tol_energy=1e-8,
              max_iter=200, max_subspace=None, precond_floor=1e-8, guess=None,
-             drop_tol=1e-12):
+             drop_tol=1e-12, correction="davidson"):
     """Block Davidson for the lowest ``nroots`` eigenpairs (Davidson 1975,
     cited in Section I; one matrix-vector product per iteration and vector,
     diagonal preconditioner and Gram-Schmidt, Section VI).
@@ -337,6 +354,10 @@ def davidson(matvec, hdiag, nroots=1, tol_residual=1e-8, tol_energy=1e-8,
       unless ``guess`` (N, k) is given;
     * correction t = r / (theta - H_II), the denominator clamped to
       sign * max(|.|, precond_floor) (sign + for a zero denominator);
+      correction="olsen" (not in the paper: J. Olsen, P. Jorgensen and
+      J. Simons, Chem. Phys. Lett. 169, 463 (1990)) takes instead
+      t = (r - eps x) / (theta - H_II) with eps = (x^T D^-1 r) / (x^T D^-1 x),
+      D the same clamped denominator, so that x^T t = 0;
     * classical Gram-Schmidt applied twice; a vector whose norm after the
       two passes is below ``drop_tol`` is dropped;
     * subspace limit max(8 * nroots, 16); on reaching it, restart from the
@@ -382,10 +403,8 @@ def davidson(matvec, hdiag, nroots=1, tol_residual=1e-8, tol_energy=1e-8,
         theta_old = theta.copy()
         T = []
         for k in np.nonzero(~conv)[0]:
-            den = theta[k] - hdiag
-            den = np.where(np.abs(den) < precond_floor,
-                           np.where(den < 0, -precond_floor, precond_floor), den)
-            T.append(R[:, k] / den)
+            T.append(correction_vector(R[:, k], X[:, k], theta[k], hdiag, precond_floor,
+                                       correction))
         nkeep = Vb.shape[1]
         if nkeep + len(T) > max_subspace:
             m = min(2 * nroots, Vb.shape[1])

@@ -67,7 +67,8 @@ class Options(ctypes.Structure):
     _fields_ = [("nroots", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("max_subspace", ctypes.c_int), ("tol_energy", ctypes.c_double),
                 ("tol_residual", ctypes.c_double), ("precond_floor", ctypes.c_double),
-                ("use_guess", ctypes.c_int), ("use_stored_h", ctypes.c_int)]
+                ("use_guess", ctypes.c_int), ("use_stored_h", ctypes.c_int),
+                ("correction", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -333,9 +334,11 @@ def sigma(ctx: Context, tables: Tables, C: torch.Tensor,
 def davidson(ctx: Context, tables: Tables, nroots: int = 1, tol_residual: float = 1e-8,
              tol_energy: float = 1e-8, max_iter: int = 200, max_subspace: int = 0,
              precond_floor: float = 1e-8, guess: Optional[torch.Tensor] = None,
-             raise_on_nonconvergence: bool = True, use_stored_h: bool = False):
+             raise_on_nonconvergence: bool = True, use_stored_h: bool = False,
+             correction: str = "davidson"):
     """sqd_davidson.  Returns (energies (numpy), C (nroots, n_alpha, n_beta)
-    tensor, iterations, residual norms (numpy), status code)."""
+    tensor, iterations, residual norms (numpy), status code).  correction:
+    "davidson" (t = r / (theta - H_II)) or "olsen" (t orthogonal to x)."""
     import numpy as np
     C = torch.zeros((nroots, tables.na, tables.nb), dtype=torch.float64,
                     device="cuda:%d" % ctx.device)
@@ -345,7 +348,8 @@ def davidson(ctx: Context, tables: Tables, nroots: int = 1, tol_residual: float 
         use_guess = 1
     o = Options(nroots=nroots, max_iter=max_iter, max_subspace=max_subspace,
                 tol_energy=tol_energy, tol_residual=tol_residual, precond_floor=precond_floor,
-                use_guess=use_guess, use_stored_h=1 if use_stored_h else 0)
+                use_guess=use_guess, use_stored_h=1 if use_stored_h else 0,
+                correction={"davidson": 0, "olsen": 1}[correction])
     e = np.zeros(nroots)
     r = np.zeros(nroots)
     it = ctypes.c_int(0)

@@ -605,6 +605,13 @@ struct dav_work {
 // twice per vector, dropping vectors below 1e-12), H applied to the block and
 // the new columns of G.  In exact arithmetic this is the same basis as
 // vector-by-vector CGS2 of the preconditioned residuals in root order.
+// Second Gram-Schmidt pass of a new block when some vector lost more than
+// this fraction of its squared norm in the first (Daniel-Gragg-Kaufman-
+// Stewart test with eta^2 = 1 - SQD_REORTH_LOSS).
+#ifndef SQD_REORTH_LOSS
+#define SQD_REORTH_LOSS 0.5
+#endif
+
 static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, double *h_energies,
                          double *d_C, int *h_iters, double *h_res) {
     cudaStream_t st = ctx->stream;
@@ -621,8 +628,11 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
     const int k2 = std::min(2 * k, M);
     const int kr = std::min(3 * k, M);  // restart basis: 2k Ritz + k previous Ritz
     dav_work w;
-    const int64_t npart = std::max<int64_t>(std::max<int64_t>((int64_t)M * nblk, (int64_t)nbd * M * k),
-                                            (int64_t)nbr * std::max(k, 1));
+    // partial sums: multidot (M x nblk), block dot (nbd x M x k), Ritz (nbr x k),
+    // preconditioner with Olsen's dots (2 x nbr + 2)
+    const int64_t npart = std::max<int64_t>(
+        std::max<int64_t>((int64_t)M * nblk, (int64_t)nbd * M * k),
+        std::max<int64_t>((int64_t)nbr * std::max(k, 1), 2LL * nbr + 2));
     SQD_TRY(dalloc(ctx, &w.Vb, (int64_t)M * N));
     SQD_TRY(dalloc(ctx, &w.Wb, (int64_t)M * N));
     SQD_TRY(dalloc(ctx, &w.X, (int64_t)k * N));
@@ -679,7 +689,7 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
                 for (int j = 0; j < b && !again; j++) {
                     double p2 = 0.0;
                     for (int i = 0; i < m0; i++) p2 += hP[i + (size_t)j * m0] * hP[i + (size_t)j * m0];
-                    again = !(p2 <= 0.5 * htn2[j]);
+                    again = !(p2 <= SQD_REORTH_LOSS * htn2[j]);
                 }
                 if (!again) break;
             }
@@ -844,9 +854,16 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
         prof_begin(ctx, PROF_DAVIDSON);
         for (int q = 0; q < b; q++) {
             const int j = todo[q];
-            SQD_TRY(launch_precondition_norm(ctx, w.R + (int64_t)j * N, t->diag, theta[j],
-                                             o->precond_floor, N, w.Vb + (int64_t)(m_old + q) * N,
-                                             w.partial, w.tn2 + q));
+            if (o->correction == 1)
+                SQD_TRY(launch_precondition_olsen(ctx, w.R + (int64_t)j * N, w.X + (int64_t)j * N,
+                                                  t->diag, theta[j], o->precond_floor, N,
+                                                  w.Vb + (int64_t)(m_old + q) * N, w.partial,
+                                                  w.tn2 + q));
+            else
+                SQD_TRY(launch_precondition_norm(ctx, w.R + (int64_t)j * N, t->diag, theta[j],
+                                                 o->precond_floor, N,
+                                                 w.Vb + (int64_t)(m_old + q) * N, w.partial,
+                                                 w.tn2 + q));
         }
         prof_end(ctx, 2.0 * b * dN, 24.0 * b * dN);
         int nacc = 0;
@@ -887,7 +904,8 @@ int sqd_davidson(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, double *h_en
     if (o->nroots < 1 || o->nroots > 32 || o->nroots > N)
         return sqd_fail(ctx, SQD_EINVAL, "nroots must be in [1, min(32, dimension)]");
     if (o->max_iter < 0 || !(o->tol_energy >= 0) || !(o->tol_residual >= 0) ||
-        !(o->precond_floor > 0) || o->max_subspace < 0)
+        !(o->precond_floor > 0) || o->max_subspace < 0 || o->correction < 0 ||
+        o->correction > 1)
         return sqd_fail(ctx, SQD_EINVAL, "invalid Davidson options");
     SQD_TRY(use_device(ctx));
     return davidson_impl(ctx, t, o, h_energies, d_C, h_iters, h_res);
@@ -948,7 +966,8 @@ int sqd_davidson_batched(sqd_ctx *ctx, int nbatch, sqd_tables *const *tables,
         return sqd_fail(ctx, SQD_EINVAL, "nbatch >= 1, tables and h_energies are required");
     if (o->nroots != 1) return sqd_fail(ctx, SQD_EINVAL, "the batched solver finds one root");
     if (o->max_iter < 0 || !(o->tol_energy >= 0) || !(o->tol_residual >= 0) ||
-        !(o->precond_floor > 0) || o->max_subspace < 0)
+        !(o->precond_floor > 0) || o->max_subspace < 0 || o->correction < 0 ||
+        o->correction > 1)
         return sqd_fail(ctx, SQD_EINVAL, "invalid Davidson options");
     for (int b = 0; b < nbatch; b++)
         if (!tables[b]) return sqd_fail(ctx, SQD_EINVAL, "tables[%d] is NULL", b);

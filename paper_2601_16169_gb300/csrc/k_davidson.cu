@@ -497,6 +497,69 @@ int launch_precondition_norm(sqd_ctx *ctx, const double *R, const double *diag, 
     return SQD_OK;
 }
 
+// Olsen's correction: with d = theta - diag (clamped as above),
+// a = sum x r / d and b = sum x x / d (per-block partials, 2 per block), then
+// T = (R - (a/b) X) / d, so that X^T T = 0, and partials of |T|^2.
+__global__ void __launch_bounds__(RED_THREADS)
+    k_olsen_dots(const double *__restrict__ R, const double *__restrict__ X,
+                 const double *__restrict__ diag, double theta, double floor_, int64_t n,
+                 double *__restrict__ partial) {
+    __shared__ double red[32];
+    double sa = 0.0, sb = 0.0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double d = theta - diag[p];
+        if (fabs(d) < floor_) d = (d < 0.0) ? -floor_ : floor_;
+        const double x = X[p];
+        sa += x * R[p] / d;
+        sb += x * x / d;
+    }
+    const double ta = block_sum(sa, red);
+    const double tb = block_sum(sb, red);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = ta;
+        partial[gridDim.x + blockIdx.x] = tb;
+    }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+    k_olsen_apply(const double *__restrict__ R, const double *__restrict__ X,
+                  const double *__restrict__ diag, double theta, double floor_, int64_t n,
+                  const double *__restrict__ ab, double *__restrict__ T,
+                  double *__restrict__ partial) {
+    __shared__ double red[32];
+    const double eps = (ab[1] != 0.0) ? ab[0] / ab[1] : 0.0;
+    double ss = 0.0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double d = theta - diag[p];
+        if (fabs(d) < floor_) d = (d < 0.0) ? -floor_ : floor_;
+        const double t = (R[p] - eps * X[p]) / d;
+        T[p] = t;
+        ss = fma(t, t, ss);
+    }
+    const double tot = block_sum(ss, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+// partial: 4 * SMs + 2 doubles; norm2 (device) = |T|^2
+int launch_precondition_olsen(sqd_ctx *ctx, const double *R, const double *X, const double *diag,
+                              double theta, double floor_, int64_t n, double *T, double *partial,
+                              double *norm2) {
+    if (n == 0) return SQD_OK;
+    const unsigned g = precondition_grid(ctx, n);
+    double *ab = partial + 2 * g;  // 2 doubles after the partials
+    k_olsen_dots<<<g, RED_THREADS, 0, ctx->stream>>>(R, X, diag, theta, floor_, n, partial);
+    SQD_LAUNCHED(ctx);
+    k_multidot_final<<<1, 64, 0, ctx->stream>>>(partial, (int)g, 2, ab);
+    SQD_LAUNCHED(ctx);
+    k_olsen_apply<<<g, RED_THREADS, 0, ctx->stream>>>(R, X, diag, theta, floor_, n, ab, T, partial);
+    SQD_LAUNCHED(ctx);
+    k_multidot_final<<<1, 64, 0, ctx->stream>>>(partial, (int)g, 1, norm2);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
 // x *= s  (invert_sqrt: x *= 1/sqrt(s))
 __global__ void k_scale(double *__restrict__ x, int64_t n, const double *__restrict__ s,
                         int invert_sqrt) {

@@ -126,7 +126,9 @@ int set_ab_groups(sqd_ctx *ctx, sqd_tables *t, double scale) {
     const spin_tables *A = &t->a;
     const int64_t target_blocks = (int64_t)(scale * 16.0 * ctx->sm_count + 0.5);
     const int64_t nch = std::max(1, t->ab.nchunks);
-    int64_t G = (target_blocks + nch - 1) / nch;
+    // round down: target_blocks is a whole number of 2-block-per-SM waves,
+    // and one block over it would cost a nearly empty extra wave
+    int64_t G = target_blocks / nch;
     if (G > A->n) G = A->n;
     if (G < 1) G = 1;
     if (G > 65535) G = 65535;

@@ -234,6 +234,9 @@ int launch_precondition(sqd_ctx *, const double *R, const double *diag, double t
 int launch_precondition_norm(sqd_ctx *, const double *R, const double *diag, double theta,
                              double floor_, int64_t n, double *T, double *partial,
                              double *norm2);
+int launch_precondition_olsen(sqd_ctx *, const double *R, const double *X, const double *diag,
+                              double theta, double floor_, int64_t n, double *T, double *partial,
+                              double *norm2);
 int launch_scale(sqd_ctx *, double *x, int64_t n, const double *s_dev, int invert_sqrt);
 int launch_jacobi_eigh(sqd_ctx *, const double *G, int ldg, int m, double *evals, double *evecs,
                        int m_old = 0, const double *E_old = nullptr,

@@ -308,6 +308,28 @@ def test_davidson_outputs_consistent_when_stopped_early(sqd, ctx):
     t.close()
 
 
+@pytest.mark.parametrize("name", ["uneven", "h2o29_70"])
+def test_davidson_olsen_vs_lapack_and_oracle(sqd, ctx, name):
+    if name == "h2o29_70":
+        w = si.workload("h2o29", n_unique=70)
+        norb, sa, na_e, sb, nb_e, h, V, ecore = w.norb, w.strings_a, 5, w.strings_b, 5, w.h, w.V, 0.0
+    else:
+        norb, sa, na_e, sb, nb_e, h, V, ecore = case(name)
+    t = make_tables(sqd, ctx, norb, sa, na_e, sb, nb_e, h, V, ecore)
+    H = oracle.dense_h(norb, h, V, ecore, sa, sb)
+    ref = np.linalg.eigvalsh(H)[:4]
+    e, X, it, res, rc = sqd.davidson(ctx, t, nroots=4, tol_residual=1e-8, tol_energy=1e-11,
+                                     correction="olsen")
+    assert rc == 0 and np.max(np.abs(e - ref)) <= 1e-9
+    Xh = X.cpu().numpy().reshape(4, -1)
+    assert np.all(np.linalg.norm(Xh @ H - e[:, None] * Xh, axis=1) <= 1e-7)
+    hd = oracle.diag(norb, h, V, ecore, sa, sb)
+    th, _, _, _, conv = oracle.davidson(lambda Y: H @ Y, hd, nroots=4, tol_residual=1e-8,
+                                        tol_energy=1e-11, correction="olsen")
+    assert conv and np.max(np.abs(e - th)) <= 1e-9
+    t.close()
+
+
 def test_davidson_matches_oracle_davidson(sqd, ctx):
     # same algorithm on the oracle side (matrix-free oracle sigma)
     w = si.workload("h2o29", n_unique=120)

@@ -278,6 +278,42 @@ def test_davidson_matches_lapack_full8():
     assert np.linalg.norm(H @ X3 - X3 * th3) <= 1e-6
 
 
+def test_olsen_correction_pins():
+    # the correction of one root, from its definition: Davidson's t solves
+    # D t = r; Olsen's t is orthogonal to x and differs from Davidson's by a
+    # multiple of D^-1 x
+    rng = np.random.default_rng(5)
+    n = 50
+    hd = np.sort(rng.normal(size=n)) * 3.0
+    x = rng.normal(size=n)
+    x /= np.linalg.norm(x)
+    r = rng.normal(size=n)
+    theta = hd[0] - 0.1
+    td = oracle.correction_vector(r, x, theta, hd)
+    assert np.allclose((theta - hd) * td, r, rtol=1e-14, atol=1e-14)
+    to = oracle.correction_vector(r, x, theta, hd, correction="olsen")
+    assert abs(x @ to) <= 1e-12 * np.linalg.norm(to)
+    dx = x / (theta - hd)
+    c = (td - to) @ dx / (dx @ dx)
+    assert np.allclose(td - to, c * dx, rtol=0, atol=1e-12 * np.linalg.norm(td))
+
+
+def test_davidson_olsen_matches_lapack():
+    w = si.workload("full8")
+    sa = sb = w.strings_a
+    H = oracle.dense_h(w.norb, w.h, w.V, 0.0, sa, sb)
+    ref = np.linalg.eigvalsh(H)[:3]
+    hd = oracle.diag(w.norb, w.h, w.V, 0.0, sa, sb)
+
+    def mv(X):
+        return oracle.sigma(w.norb, w.h, w.V, 0.0, sa, sb, X.T).T
+
+    th, X, it, rn, conv = oracle.davidson(mv, hd, nroots=3, tol_residual=1e-7,
+                                          tol_energy=1e-12, correction="olsen")
+    assert conv and np.max(np.abs(th - ref)) <= 1e-10
+    assert np.linalg.norm(H @ X - X * th) <= 1e-6
+
+
 # ---------------------------------------------------------------- RDMs -----
 
 def _tiny_state(seed=0, norb=4, na_e=2, nb_e=2, k=None):
