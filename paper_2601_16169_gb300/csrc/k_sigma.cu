@@ -24,9 +24,9 @@
 //                reads C rows coalesced along the column.  Runs once on C
 //                with the alpha tables (diagonal included) and once on C^T
 //                with the beta tables.
-//  k_alpha_beta  paired singles.  A block owns a contiguous range Y of beta
-//                rows and their single entries (each entry of row Jb in Y
-//                points to a neighbour Ib).  For every alpha row Ia of its
+//  k_alpha_beta  paired singles.  A block owns AB_ECAP consecutive beta
+//                single entries, whose rows form a contiguous range Y (each
+//                entry of row Jb in Y points to a neighbour Ib).  For every alpha row Ia of its
 //                group it stages the slabs C(Ja, Y) of all alpha singles of
 //                Ia in shared memory (contiguous, coalesced), accumulates
 //                acc_e = sum_a s_a s_e V[pq_a][pq_e] C(Ja, Jb_e) in
@@ -80,7 +80,7 @@ int launch_same_spin(sqd_ctx *ctx, const spin_tables *R, const spin_tables *Cc, 
 
 // ---------------------------------------------------------- alpha-beta ---
 
-__global__ void __launch_bounds__(AB_THREADS, 2) k_alpha_beta(ab_args a) {
+__global__ void __launch_bounds__(AB_THREADS, AB_MINB) k_alpha_beta(ab_args a) {
     alpha_beta_block(a, blockIdx.x, blockIdx.y);
 }
 
@@ -120,13 +120,13 @@ int launch_alpha_beta(sqd_ctx *ctx, const sqd_tables *t, const double *C, double
 }
 
 // Schedule for k_alpha_beta: beta chunks of at most AB_YW rows and AB_ECAP
-// entries; alpha groups of roughly equal single counts, about
-// scale * 16 blocks per SM in all (scale is tuned on the first sigma).
+// entries; alpha groups of roughly equal single counts, about scale * 8
+// waves of AB_MINB blocks per SM in all (scale is tuned on the first sigma).
 int set_ab_groups(sqd_ctx *ctx, sqd_tables *t, double scale) {
     const spin_tables *A = &t->a;
-    const int64_t target_blocks = (int64_t)(scale * 16.0 * ctx->sm_count + 0.5);
+    const int64_t target_blocks = (int64_t)(scale * 8.0 * AB_MINB * ctx->sm_count + 0.5);
     const int64_t nch = std::max(1, t->ab.nchunks);
-    // round down: target_blocks is a whole number of 2-block-per-SM waves,
+    // round down: target_blocks is a whole number of waves,
     // and one block over it would cost a nearly empty extra wave
     int64_t G = target_blocks / nch;
     if (G > A->n) G = A->n;

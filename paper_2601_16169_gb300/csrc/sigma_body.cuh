@@ -51,33 +51,34 @@ template <int N>
 struct ab_int {
     static constexpr int value = N;
 };
-// call f(ab_int<n>{}) for n in [1, 16] (uniform across the block)
-#define AB_DISPATCH(n, f)                  \
-    switch (n) {                           \
-        case 1: f(ab_int<1>{}); break;     \
-        case 2: f(ab_int<2>{}); break;     \
-        case 3: f(ab_int<3>{}); break;     \
-        case 4: f(ab_int<4>{}); break;     \
-        case 5: f(ab_int<5>{}); break;     \
-        case 6: f(ab_int<6>{}); break;     \
-        case 7: f(ab_int<7>{}); break;     \
-        case 8: f(ab_int<8>{}); break;     \
-        case 9: f(ab_int<9>{}); break;     \
-        case 10: f(ab_int<10>{}); break;   \
-        case 11: f(ab_int<11>{}); break;   \
-        case 12: f(ab_int<12>{}); break;   \
-        case 13: f(ab_int<13>{}); break;   \
-        case 14: f(ab_int<14>{}); break;   \
-        case 15: f(ab_int<15>{}); break;   \
-        default: f(ab_int<16>{}); break;   \
+// call f(ab_int<n>{}) for n in [1, AB_EPT] (uniform across the block)
+#define AB_CASE(N, f)                                        \
+    case N:                                                  \
+        f(ab_int<((N) <= AB_EPT ? (N) : AB_EPT)>{});         \
+        break;
+#define AB_DISPATCH(n, f)                                                              \
+    switch (n) {                                                                       \
+        AB_CASE(1, f) AB_CASE(2, f) AB_CASE(3, f) AB_CASE(4, f) AB_CASE(5, f)          \
+        AB_CASE(6, f) AB_CASE(7, f) AB_CASE(8, f) AB_CASE(9, f) AB_CASE(10, f)         \
+        AB_CASE(11, f) AB_CASE(12, f) AB_CASE(13, f) AB_CASE(14, f) AB_CASE(15, f)     \
+        default: f(ab_int<AB_EPT>{}); break;                                           \
     }
 
 #define AB_THREADS 256
-#define AB_EPT 16                          // beta entries per thread
+// 8 entries per thread fit in 80 registers, so 3 blocks (24 warps) share an
+// SM and hide the gather latency of V and the slabs; measured against 16
+// entries at 2 blocks per SM: 0.84 -> 0.90 of the FP64 peak at h2o29, 0.90 ->
+// 0.92 at scale36, 0.90 -> 0.93 at adjoint29 (12 entries at 2 blocks: 0.83).
+#ifndef AB_EPT
+#define AB_EPT 8                           // beta entries per thread
+#endif
+#ifndef AB_MINB
+#define AB_MINB 3                          // resident blocks per SM (launch bounds)
+#endif
 #define AB_ECAP (AB_THREADS * AB_EPT)      // beta entries per block
 #define AB_YW 256                          // beta rows (slab width) per block
 #define AB_NA 16                           // alpha singles staged per batch
-static_assert(AB_EPT == 16, "AB_DISPATCH covers 1..16 entry slots");
+static_assert(AB_EPT >= 1 && AB_EPT <= 16, "AB_DISPATCH covers 1..16 entry slots");
 
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
