@@ -123,7 +123,9 @@ __global__ void __launch_bounds__(256) kb_transpose(const bdesc *__restrict__ D,
     }
 }
 
-__global__ void __launch_bounds__(AB_THREADS, AB_MINB) kb_alpha_beta(const bdesc *__restrict__ D,
+// persistent: 2 blocks per SM, so the per-item state of the work queue does
+// not spill at the register cap of 3 blocks per SM
+__global__ void __launch_bounds__(AB_THREADS, 2) kb_alpha_beta(const bdesc *__restrict__ D,
                                                                const bstate *__restrict__ S,
                                                                const int64_t *__restrict__ pre,
                                                                int nprob,
