@@ -123,9 +123,12 @@ __global__ void __launch_bounds__(256) kb_transpose(const bdesc *__restrict__ D,
     }
 }
 
-// persistent: 2 blocks per SM, so the per-item state of the work queue does
-// not spill at the register cap of 3 blocks per SM
-__global__ void __launch_bounds__(AB_THREADS, 2) kb_alpha_beta(const bdesc *__restrict__ D,
+// persistent, KB_AB_MINB blocks per SM: at 2 the per-item state of the work
+// queue does not spill, as it does at the register cap of 3 blocks per SM
+#ifndef KB_AB_MINB
+#define KB_AB_MINB 2
+#endif
+__global__ void __launch_bounds__(AB_THREADS, KB_AB_MINB) kb_alpha_beta(const bdesc *__restrict__ D,
                                                                const bstate *__restrict__ S,
                                                                const int64_t *__restrict__ pre,
                                                                int nprob,
@@ -589,7 +592,7 @@ static int launch_sigma_stages(sqd_ctx *ctx, batched_plan &p) {
                                                              p.counters + 1);
     SQD_LAUNCHED(ctx);
     const size_t shm = sizeof(double) * 2 * AB_NA * AB_YW;
-    kb_alpha_beta<<<2 * sm, AB_THREADS, shm, ctx->stream>>>(p.D, p.S, p.pre_ab, n,
+    kb_alpha_beta<<<KB_AB_MINB * sm, AB_THREADS, shm, ctx->stream>>>(p.D, p.S, p.pre_ab, n,
                                                              p.counters + 2);
     SQD_LAUNCHED(ctx);
     kb_same_spin<false><<<8 * sm, 256, 0, ctx->stream>>>(p.D, p.S, p.pre_ssb, n,

@@ -366,6 +366,15 @@ def test_davidson_h2o29_eight_roots(sqd, ctx):
 
 # ------------------------------------------------------------- errors ----
 
+def test_fp64_probes(sqd, ctx):
+    # the FP64 rates the roofline is read against: positive, and not above
+    # the nominal 4 flop/clk/SM of the FP64 pipe at the highest SM clock
+    dfma, dmma = ctx.measure_fp64_peaks()
+    props = torch.cuda.get_device_properties(0)
+    bound = props.multi_processor_count * 4 * 2.2e9 / 1e12
+    assert 0.0 < dfma <= bound and 0.0 < dmma <= 4 * bound
+
+
 def test_errors_are_status_codes(sqd, ctx):
     norb, sa, na_e, sb, nb_e, h, V, ecore = case("uneven")
     bad_count = np.unique(np.append(sa, np.uint64(0b111111)))  # a 6-electron string
