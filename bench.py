@@ -462,9 +462,10 @@ def run_batched(args, rank, world, local_rank):
     h = torch.from_numpy(subs[0].h).to(dev)
     V = torch.from_numpy(subs[0].V).to(dev)
     raws = [torch.from_numpy(w.raw_a.view(np.int64).copy()).to(dev) for w in subs]
-    # residuals to 1e-7: the batched and the sequential energies then agree to
-    # 1e-12 (an energy error is of order |r|^2 / gap)
-    opts = dict(tol_residual=1e-7, tol_energy=1e-8, max_iter=300)
+    # the batched and the sequential energies agree to about 6e-12 Ha (2e-13
+    # relative) whether residuals stop at 1e-6 or 1e-7: the difference is
+    # rounding along the two restart paths, not convergence
+    opts = dict(tol_residual=1e-6, tol_energy=1e-8, max_iter=300)
 
     def tables():
         out = []
@@ -518,7 +519,7 @@ def run_batched(args, rank, world, local_rank):
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
            "higher_is_better": True, "dtype": "f64",
            "config": {"workload": "%d subspaces, norb=29, 5+5 electrons, 200-3000 strings each "
-                                  "(%.3g determinants in total), ground states, ||r|| <= 1e-7"
+                                  "(%.3g determinants in total), ground states, ||r|| <= 1e-6"
                                   % (len(subs), float(np.sum(ndet)))},
            "sequential_ms": ms_s, "speedup_vs_sequential": ms_s / ms_b,
            "max_abs_energy_diff_vs_sequential": float(np.max(np.abs(np.asarray(e_b) - e_s))),
