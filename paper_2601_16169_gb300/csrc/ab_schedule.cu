@@ -54,8 +54,39 @@ __global__ void k_row_index(const int64_t *__restrict__ off, int64_t n, int32_t 
     for (int64_t e = off[r] + (threadIdx.x & 31); e < off[r + 1]; e += 32) out[e] = (int32_t)r;
 }
 
+// beta chunks of `cap` consecutive single entries (a row may be split between
+// chunks), cut earlier where they would span more than AB_YW rows; device
+// arrays of the entry bounds (n+1) and of the [first, end) rows (2n)
+static int build_chunks(sqd_ctx *ctx, sqd_tables *t, int64_t cap, int *n_out, int64_t **ce_out,
+                        int64_t **cy_out) {
+    const std::vector<int64_t> &bo = t->b->h_off1;
+    const int64_t nb = t->b->n, nnz = bo[nb];
+    std::vector<int64_t> ce{0}, cy;
+    int64_t e = 0, r = 0;
+    while (e < nnz) {
+        while (bo[r + 1] <= e) r++;  // row of entry e
+        int64_t end = std::min<int64_t>(e + cap, nnz);
+        if (r + AB_YW < nb && bo[r + AB_YW] < end) end = bo[r + AB_YW];
+        int64_t r2 = r;
+        while (bo[r2 + 1] < end) r2++;  // row of entry end-1
+        cy.push_back(r);
+        cy.push_back(r2 + 1);
+        ce.push_back(end);
+        e = end;
+    }
+    *n_out = (int)cy.size() / 2;
+    SQD_CUDA(ctx, cudaMalloc((void **)ce_out, sizeof(int64_t) * ce.size()));
+    SQD_CUDA(ctx, cudaMalloc((void **)cy_out, sizeof(int64_t) * (cy.size() + 2)));
+    SQD_CUDA(ctx, cudaMemcpy(*ce_out, ce.data(), sizeof(int64_t) * ce.size(),
+                             cudaMemcpyHostToDevice));
+    if (!cy.empty())
+        SQD_CUDA(ctx, cudaMemcpy(*cy_out, cy.data(), sizeof(int64_t) * cy.size(),
+                                 cudaMemcpyHostToDevice));
+    t->bytes += sizeof(int64_t) * (ce.size() + cy.size() + 2);
+    return SQD_OK;
+}
+
 int build_ab_schedule(sqd_ctx *ctx, sqd_tables *t) {
-    const spin_tables *B = t->b;
     spin_tables *A = &t->a;
     if (!A->src1) {
         SQD_CUDA(ctx, cudaMalloc((void **)&A->src1, sizeof(int32_t) * (A->nnz1 + 1)));
@@ -65,32 +96,9 @@ int build_ab_schedule(sqd_ctx *ctx, sqd_tables *t) {
             SQD_LAUNCHED(ctx);
         }
     }
-    // beta chunks: AB_ECAP consecutive single entries (a row may be split
-    // between chunks), cut earlier where they would span more than AB_YW rows
-    const std::vector<int64_t> &bo = B->h_off1;
-    const int64_t nb = B->n, nnz = bo[nb];
-    std::vector<int64_t> ce{0}, cy;
-    int64_t e = 0, r = 0;
-    while (e < nnz) {
-        while (bo[r + 1] <= e) r++;  // row of entry e
-        int64_t end = std::min<int64_t>(e + AB_ECAP, nnz);
-        if (r + AB_YW < nb && bo[r + AB_YW] < end) end = bo[r + AB_YW];
-        int64_t r2 = r;
-        while (bo[r2 + 1] < end) r2++;  // row of entry end-1
-        cy.push_back(r);
-        cy.push_back(r2 + 1);
-        ce.push_back(end);
-        e = end;
-    }
-    t->ab.nchunks = (int)cy.size() / 2;
-    SQD_CUDA(ctx, cudaMalloc((void **)&t->ab.chunk_e, sizeof(int64_t) * ce.size()));
-    SQD_CUDA(ctx, cudaMalloc((void **)&t->ab.chunk_y, sizeof(int64_t) * (cy.size() + 2)));
-    SQD_CUDA(ctx, cudaMemcpy(t->ab.chunk_e, ce.data(), sizeof(int64_t) * ce.size(),
-                             cudaMemcpyHostToDevice));
-    if (!cy.empty())
-        SQD_CUDA(ctx, cudaMemcpy(t->ab.chunk_y, cy.data(), sizeof(int64_t) * cy.size(),
-                                 cudaMemcpyHostToDevice));
-    t->bytes += sizeof(int64_t) * (ce.size() + cy.size() + 2);
+    SQD_TRY(build_chunks(ctx, t, AB_ECAP, &t->ab.nchunks, &t->ab.chunk_e, &t->ab.chunk_y));
+    SQD_TRY(build_chunks(ctx, t, AB_ECAP_WIDE, &t->ab.nchunks_wide, &t->ab.chunk_e_wide,
+                         &t->ab.chunk_y_wide));
     return set_ab_groups(ctx, t, 1.0);
 }
 

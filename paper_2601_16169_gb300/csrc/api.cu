@@ -421,6 +421,7 @@ void sqd_free_tables(sqd_tables *t) {
     free_spin(&t->a);
     if (!t->shared) free_spin(&t->b_own);
     void *ptrs[] = {t->h,         t->V,          t->diag,       t->ab.chunk_e, t->ab.chunk_y,
+                    t->ab.chunk_e_wide, t->ab.chunk_y_wide,
                     t->ab.group_rows, t->scratch_t, t->scratch_s, t->rdm_iket,
                     t->rdm_ibra,  t->rdm_ipq,    t->rdm_chunks, t->rdm_groups,
                     t->st_rowptr, t->st_col,     t->st_val,  t->Vf,

@@ -123,8 +123,10 @@ __global__ void __launch_bounds__(256) kb_transpose(const bdesc *__restrict__ D,
     }
 }
 
-// persistent, KB_AB_MINB blocks per SM: at 2 the per-item state of the work
-// queue does not spill, as it does at the register cap of 3 blocks per SM
+// persistent, KB_AB_MINB blocks per SM, AB_EPT_WIDE entries per thread over
+// the tables' wide chunks: with 2 blocks per SM the work-queue state and 16
+// entries fit the registers (8 entries at 3 blocks per SM spilled here and
+// ran slower)
 #ifndef KB_AB_MINB
 #define KB_AB_MINB 2
 #endif
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(AB_THREADS, KB_AB_MINB) kb_alpha_beta(const bd
         a.C = d.V + slot;
         a.S = d.W + slot;
         const int64_t local = item - pre[b];
-        alpha_beta_block(a, local % d.nch, local / d.nch);
+        alpha_beta_block_t<AB_EPT_WIDE>(a, local % d.nch, local / d.nch);
     }
 }
 
@@ -729,7 +731,10 @@ int davidson_batched_impl(sqd_ctx *ctx, int nprob, sqd_tables *const *tables,
         d.ssa = make_ss_args(&t->a, t->b, d.na, d.nb, nullptr, nullptr, t->diag);
         d.ssb = make_ss_args(t->b, &t->a, d.nb, d.na, nullptr, nullptr, nullptr);
         d.ab = make_ab_args(t, nullptr, nullptr);
-        d.nch = t->ab.nchunks;
+        // the persistent kernel runs 2 blocks per SM with 16 entries per thread
+        d.ab.chunk_e = t->ab.chunk_e_wide;
+        d.ab.chunk_y = t->ab.chunk_y_wide;
+        d.nch = t->ab.nchunks_wide;
         d.ngr = t->ab.ngroups;
         pssa.push_back(pssa.back() + d.na * ((d.nb + 255) / 256));
         pssb.push_back(pssb.back() + d.nb * ((d.na + 255) / 256));

@@ -427,27 +427,6 @@ int launch_project_g(sqd_ctx *ctx, double *G, int ldg, int m, const double *Z, i
     return SQD_OK;
 }
 
-// R_j = WY_j - theta_j X_j
-__global__ void k_residual(const double *__restrict__ X, const double *__restrict__ WY,
-                           const double *__restrict__ theta, int k, int64_t n,
-                           double *__restrict__ R) {
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n * k;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        int j = (int)(p / n);
-        R[p] = fma(-theta[j], X[p], WY[p]);
-    }
-}
-
-int launch_residual(sqd_ctx *ctx, const double *X, const double *WY, const double *theta,
-                    int k, int64_t n, double *R) {
-    if (k == 0 || n == 0) return SQD_OK;
-    unsigned g = grid_1d(n * k, 256);
-    if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
-    k_residual<<<g, 256, 0, ctx->stream>>>(X, WY, theta, k, n, R);
-    SQD_LAUNCHED(ctx);
-    return SQD_OK;
-}
-
 // T = R / (theta - diag), |denominator| clamped to floor_ (sign kept, + for 0);
 // with partial != NULL also per-block partial sums of T^2
 __global__ void __launch_bounds__(RED_THREADS)
@@ -475,16 +454,7 @@ static unsigned precondition_grid(const sqd_ctx *ctx, int64_t n) {
     return g;
 }
 
-int launch_precondition(sqd_ctx *ctx, const double *R, const double *diag, double theta,
-                        double floor_, int64_t n, double *T) {
-    if (n == 0) return SQD_OK;
-    k_precondition<<<precondition_grid(ctx, n), RED_THREADS, 0, ctx->stream>>>(
-        R, diag, theta, floor_, n, T, nullptr);
-    SQD_LAUNCHED(ctx);
-    return SQD_OK;
-}
-
-// the same, and *norm2 (device) = |T|^2; partial holds 4 * SMs doubles
+// T = R / (theta - diag) and *norm2 (device) = |T|^2; partial holds 4 * SMs doubles
 int launch_precondition_norm(sqd_ctx *ctx, const double *R, const double *diag, double theta,
                              double floor_, int64_t n, double *T, double *partial,
                              double *norm2) {

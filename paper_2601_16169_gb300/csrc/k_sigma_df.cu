@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(AB_THREADS, AB_MINB)
                 }
             }
         };
-        AB_DISPATCH(nk, pairs);
+        AB_DISPATCH(nk, pairs, AB_EPT);
         __syncthreads();
         buf ^= 1;
     }

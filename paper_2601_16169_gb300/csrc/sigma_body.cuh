@@ -51,24 +51,25 @@ template <int N>
 struct ab_int {
     static constexpr int value = N;
 };
-// call f(ab_int<n>{}) for n in [1, AB_EPT] (uniform across the block)
-#define AB_CASE(N, f)                                        \
+// call f(ab_int<n>{}) for n in [1, M] (uniform across the block), M <= 16
+#define AB_CASE(N, f, M)                                     \
     case N:                                                  \
-        f(ab_int<((N) <= AB_EPT ? (N) : AB_EPT)>{});         \
+        f(ab_int<((N) <= (M) ? (N) : (M))>{});               \
         break;
-#define AB_DISPATCH(n, f)                                                              \
-    switch (n) {                                                                       \
-        AB_CASE(1, f) AB_CASE(2, f) AB_CASE(3, f) AB_CASE(4, f) AB_CASE(5, f)          \
-        AB_CASE(6, f) AB_CASE(7, f) AB_CASE(8, f) AB_CASE(9, f) AB_CASE(10, f)         \
-        AB_CASE(11, f) AB_CASE(12, f) AB_CASE(13, f) AB_CASE(14, f) AB_CASE(15, f)     \
-        default: f(ab_int<AB_EPT>{}); break;                                           \
+#define AB_DISPATCH(n, f, M)                                                                   \
+    switch (n) {                                                                               \
+        AB_CASE(1, f, M) AB_CASE(2, f, M) AB_CASE(3, f, M) AB_CASE(4, f, M) AB_CASE(5, f, M)   \
+        AB_CASE(6, f, M) AB_CASE(7, f, M) AB_CASE(8, f, M) AB_CASE(9, f, M) AB_CASE(10, f, M)  \
+        AB_CASE(11, f, M) AB_CASE(12, f, M) AB_CASE(13, f, M) AB_CASE(14, f, M)                \
+        AB_CASE(15, f, M)                                                                      \
+        default: f(ab_int<(M)>{}); break;                                                      \
     }
 
-#define AB_THREADS 256
 // 8 entries per thread fit in 80 registers, so 3 blocks (24 warps) share an
 // SM and hide the gather latency of V and the slabs; measured against 16
 // entries at 2 blocks per SM: 0.84 -> 0.90 of the FP64 peak at h2o29, 0.90 ->
 // 0.92 at scale36, 0.90 -> 0.93 at adjoint29 (12 entries at 2 blocks: 0.83).
+#define AB_THREADS 256
 #ifndef AB_EPT
 #define AB_EPT 8                           // beta entries per thread
 #endif
@@ -79,6 +80,8 @@ struct ab_int {
 #define AB_YW 256                          // beta rows (slab width) per block
 #define AB_NA 16                           // alpha singles staged per batch
 static_assert(AB_EPT >= 1 && AB_EPT <= 16, "AB_DISPATCH covers 1..16 entry slots");
+#define AB_EPT_WIDE 16                     // entries per thread of the batched kernel
+#define AB_ECAP_WIDE (AB_THREADS * AB_EPT_WIDE)
 
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -123,7 +126,8 @@ __device__ __forceinline__ void same_spin_tile(const ss_args &a, int64_t row, in
 
 // One block's work of the paired-singles product: beta chunk `chunk`,
 // alpha row group `group` (dynamic shared memory: 2*AB_NA*AB_YW doubles).
-__device__ __forceinline__ void alpha_beta_block(const ab_args &a, int64_t chunk, int64_t group) {
+template <int EPT>
+__device__ __forceinline__ void alpha_beta_block_t(const ab_args &a, int64_t chunk, int64_t group) {
     // double-buffered slabs in dynamic shared memory: [2][AB_NA][AB_YW] doubles
     extern __shared__ double ab_dyn[];
     double(*slab)[AB_NA][AB_YW] = reinterpret_cast<double(*)[AB_NA][AB_YW]>(ab_dyn);
@@ -144,11 +148,11 @@ __device__ __forceinline__ void alpha_beta_block(const ab_args &a, int64_t chunk
 
     // this thread's beta entries: neighbour Ib and packed
     // (V column | slab column << 12 | sign << 31)
-    int32_t ib[AB_EPT];
-    uint32_t info[AB_EPT];
-    double acc[AB_EPT];
+    int32_t ib[EPT];
+    uint32_t info[EPT];
+    double acc[EPT];
 #pragma unroll
-    for (int k = 0; k < AB_EPT; k++) {
+    for (int k = 0; k < EPT; k++) {
         int64_t e = e0 + tid + (int64_t)k * AB_THREADS;
         ib[k] = -1;
         info[k] = 0;
@@ -183,7 +187,7 @@ __device__ __forceinline__ void alpha_beta_block(const ab_args &a, int64_t chunk
     };
     auto flush = [&](int64_t row) {
 #pragma unroll
-        for (int k = 0; k < AB_EPT; k++) {
+        for (int k = 0; k < EPT; k++) {
             if (ib[k] >= 0) atomicAdd(&a.S[row * a.nb + ib[k]], acc[k]);
             acc[k] = 0.0;
         }
@@ -219,12 +223,17 @@ __device__ __forceinline__ void alpha_beta_block(const ab_args &a, int64_t chunk
                 }
             }
         };
-        AB_DISPATCH(nk, pairs);
+        AB_DISPATCH(nk, pairs, EPT);
         __syncthreads();  // buffer `buf` is reused by the batch after next
         buf ^= 1;
     }
     if (row_cur >= 0) flush(row_cur);
     cp_async_wait<0>();
+}
+
+// the sigma kernel's block: AB_EPT entries per thread, chunks of AB_ECAP entries
+__device__ __forceinline__ void alpha_beta_block(const ab_args &a, int64_t chunk, int64_t group) {
+    alpha_beta_block_t<AB_EPT>(a, chunk, group);
 }
 
 // out[c][r] (+)= in[r][c] for one 32 x 32 tile at (row r0, column c0); in is

@@ -94,6 +94,10 @@ struct ab_schedule {
     int nchunks = 0;
     int64_t *chunk_e = nullptr;  // device, nchunks+1: entry ranges of the beta singles
     int64_t *chunk_y = nullptr;  // device, 2*nchunks: [first, end) beta rows of each chunk
+    // the same for the wider chunks of the batched kernel (AB_ECAP_WIDE entries)
+    int nchunks_wide = 0;
+    int64_t *chunk_e_wide = nullptr;
+    int64_t *chunk_y_wide = nullptr;
     // alpha row groups: [grp[g], grp[g+1])
     int ngroups = 0;
     int64_t *group_rows = nullptr;  // device, ngroups+1
@@ -227,10 +231,6 @@ int launch_ritz_block(sqd_ctx *, const double *V, const double *W, int64_t ld, i
                       double *R, int64_t n, double *partial, int nblk, double *rnorm2);
 int launch_project_g(sqd_ctx *, double *G, int ldg, int m, const double *Z, int ldz, int r,
                      double *GZ);
-int launch_residual(sqd_ctx *, const double *X, const double *WY, const double *theta,
-                    int k, int64_t n, double *R);
-int launch_precondition(sqd_ctx *, const double *R, const double *diag, double theta,
-                        double floor_, int64_t n, double *T);
 int launch_precondition_norm(sqd_ctx *, const double *R, const double *diag, double theta,
                              double floor_, int64_t n, double *T, double *partial,
                              double *norm2);

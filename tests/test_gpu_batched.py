@@ -41,9 +41,11 @@ def _compare(sqd, ctx, subs, tol_r=1e-8):
     assert device_loop  # the iteration loop ran inside one graph
     for b, t in enumerate(tabs):
         e1, X1, _, _, _ = sqd.davidson(ctx, t, nroots=1, tol_residual=tol_r, tol_energy=1e-10)
-        # the two solvers differ only in summation order and restart path:
-        # agreement to 1e-12 Ha plus a few hundred ulps of |E| (~30 Ha here)
-        assert abs(e[b] - e1[0]) <= 1e-12 + 1e-13 * abs(e1[0]), (b, e[b], e1[0])
+        # the two solvers differ only in summation order and restart path
+        # (projected matrices rebuilt as Z^T G Z over hundreds of iterations):
+        # agreement to 1e-12 Ha plus 2e-13 of |E| (30-40 Ha here), the same at
+        # residuals of 1e-6 and 1e-7, so rounding and not convergence
+        assert abs(e[b] - e1[0]) <= 1e-12 + 2e-13 * abs(e1[0]), (b, e[b], e1[0])
         ov = abs(float((Cs[b].reshape(-1) * X1[0].reshape(-1)).sum()))
         assert ov >= 1 - 1e-8
         assert abs(float(Cs[b].norm()) - 1.0) <= 1e-12
