@@ -160,6 +160,20 @@ def cpu_baseline(w, rows_n):
             "seconds": dt}
 
 
+def cpu_baseline_one_thread(name, rows_n):
+    """The same oracle sample on one host thread (a child process started
+    with OMP_NUM_THREADS=1, so this process's OpenMP pool is untouched)."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench, sqd_inputs as si; "
+            "print(json.dumps(bench.cpu_baseline(si.workload(%r), %d)))" % (ROOT, name, rows_n))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True,
+                             text=True, timeout=300)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as exc:  # reported, not fatal: the bench line stays valid
+        return {"error": str(exc)[:200]}
+
+
 def default_cpu_rows(name):
     return {"scale36": 400000, "h2o29": 4000000, "adjoint29": 2000000, "full8": 4900}[name]
 
@@ -375,6 +389,8 @@ def run_ours(args, rank, world, local_rank):
                                                       "clocks")}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_rows or default_cpu_rows(args.workload))
+        line["cpu_baseline_1thread"] = cpu_baseline_one_thread(
+            args.workload, max(1000, (args.cpu_rows or default_cpu_rows(args.workload)) // 100))
     return line
 
 
