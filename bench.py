@@ -83,6 +83,9 @@ def _args():
                    help="0: native FP64 sigma (headline); 1: double-float on the FP32 pipe")
     p.add_argument("--correction", default="davidson", choices=["davidson", "olsen"],
                    help="Davidson correction vector (olsen: orthogonal to the Ritz vector)")
+    p.add_argument("--max-iter", type=int, default=None,
+                   help="stop Davidson after this many iterations (short profiling runs; "
+                        "the line then reports an unconverged solve)")
     p.add_argument("--max-subspace", type=int, default=None,
                    help="Davidson subspace limit (default max(8 nroots, 16))")
     p.add_argument("--stored", action="store_true",
@@ -233,6 +236,9 @@ def run_ours(args, rank, world, local_rank):
     opts = dict(SOLVE[args.workload])
     if args.max_subspace:
         opts["max_subspace"] = args.max_subspace
+    if args.max_iter is not None:
+        opts["max_iter"] = args.max_iter
+        opts["raise_on_nonconvergence"] = False
     if args.correction != "davidson":
         opts["correction"] = args.correction
     ctx = sqd.Context(local_rank)
