@@ -100,59 +100,61 @@ __device__ __forceinline__ void combine_group(const double *__restrict__ A, int6
     }
 }
 
+// one kernel per group width, so that a narrow group (one root, one new
+// vector) is not held to the register count of the widest and runs at the
+// occupancy its HBM streaming needs
+template <int JN>
 __global__ void __launch_bounds__(256) k_combine(const double *__restrict__ A, int64_t lda, int m,
-                                                 const double *__restrict__ Y, int ldy, int k,
-                                                 double *__restrict__ out, int64_t ldo, int64_t n,
+                                                 const double *__restrict__ Yj, int ldy,
+                                                 double *__restrict__ oj, int64_t ldo, int64_t n,
                                                  int sub) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        for (int j0 = 0; j0 < k; j0 += 8) {
-            const double *Yj = Y + (int64_t)j0 * ldy;
-            double *oj = out + (int64_t)j0 * ldo;
-            switch (min(8, k - j0)) {  // uniform across the grid
-                case 1: combine_group<1>(A, lda, m, Yj, ldy, oj, ldo, p, sub); break;
-                case 2: combine_group<2>(A, lda, m, Yj, ldy, oj, ldo, p, sub); break;
-                case 3: combine_group<3>(A, lda, m, Yj, ldy, oj, ldo, p, sub); break;
-                case 4: combine_group<4>(A, lda, m, Yj, ldy, oj, ldo, p, sub); break;
-                case 5: combine_group<5>(A, lda, m, Yj, ldy, oj, ldo, p, sub); break;
-                case 6: combine_group<6>(A, lda, m, Yj, ldy, oj, ldo, p, sub); break;
-                case 7: combine_group<7>(A, lda, m, Yj, ldy, oj, ldo, p, sub); break;
-                default: combine_group<8>(A, lda, m, Yj, ldy, oj, ldo, p, sub); break;
-            }
+         p += (int64_t)gridDim.x * blockDim.x)
+        combine_group<JN>(A, lda, m, Yj, ldy, oj, ldo, p, sub);
+}
+
+// out_j (-)= sum_i A_i Y_ij for j < k, one launch per group of 8 outputs
+static int combine_launch(sqd_ctx *ctx, const double *A, int64_t lda, int m, const double *Y,
+                          int ldy, int k, double *out, int64_t ldo, int64_t n, int sub) {
+    if (k == 0 || n == 0) return SQD_OK;
+    unsigned g = grid_1d(n, 256);
+    if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
+    for (int j0 = 0; j0 < k; j0 += 8) {
+        const double *Yj = Y + (int64_t)j0 * ldy;
+        double *oj = out + (int64_t)j0 * ldo;
+        cudaStream_t st = ctx->stream;
+        switch (min(8, k - j0)) {
+            case 1: k_combine<1><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub); break;
+            case 2: k_combine<2><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub); break;
+            case 3: k_combine<3><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub); break;
+            case 4: k_combine<4><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub); break;
+            case 5: k_combine<5><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub); break;
+            case 6: k_combine<6><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub); break;
+            case 7: k_combine<7><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub); break;
+            default: k_combine<8><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub); break;
         }
+        SQD_LAUNCHED(ctx);
     }
+    return SQD_OK;
 }
 
 int launch_combine(sqd_ctx *ctx, const double *A, int64_t lda, int m, const double *Y, int ldy,
                    int k, double *out, int64_t ldo, int64_t n) {
-    if (k == 0 || n == 0) return SQD_OK;
-    unsigned g = grid_1d(n, 256);
-    if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
-    k_combine<<<g, 256, 0, ctx->stream>>>(A, lda, m, Y, ldy, k, out, ldo, n, 0);
-    SQD_LAUNCHED(ctx);
-    return SQD_OK;
+    return combine_launch(ctx, A, lda, m, Y, ldy, k, out, ldo, n, 0);
 }
 
 // x[n] -= sum_i A_i[n] c[i]: one Gram-Schmidt update
 int launch_gemv_sub(sqd_ctx *ctx, const double *A, int64_t lda, int m, const double *c,
                     double *x, int64_t n) {
-    if (m == 0 || n == 0) return SQD_OK;
-    unsigned g = grid_1d(n, 256);
-    if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
-    k_combine<<<g, 256, 0, ctx->stream>>>(A, lda, m, c, m, 1, x, n, n, 1);
-    SQD_LAUNCHED(ctx);
-    return SQD_OK;
+    if (m == 0) return SQD_OK;
+    return combine_launch(ctx, A, lda, m, c, m, 1, x, n, n, 1);
 }
 
 // out_j[n] -= sum_i A_i[n] Y[i + j*ldy], j < k: the update of block Gram-Schmidt
 int launch_combine_sub(sqd_ctx *ctx, const double *A, int64_t lda, int m, const double *Y,
                        int ldy, int k, double *out, int64_t ldo, int64_t n) {
-    if (k == 0 || m == 0 || n == 0) return SQD_OK;
-    unsigned g = grid_1d(n, 256);
-    if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
-    k_combine<<<g, 256, 0, ctx->stream>>>(A, lda, m, Y, ldy, k, out, ldo, n, 1);
-    SQD_LAUNCHED(ctx);
-    return SQD_OK;
+    if (m == 0) return SQD_OK;
+    return combine_launch(ctx, A, lda, m, Y, ldy, k, out, ldo, n, 1);
 }
 
 // ------------------------------------------------- block dot products ---
@@ -335,35 +337,21 @@ __device__ __forceinline__ void ritz_group(const double *__restrict__ V,
     }
 }
 
+template <int JN>
 __global__ void __launch_bounds__(RED_THREADS)
     k_ritz_block(const double *__restrict__ V, const double *__restrict__ W, int64_t ld, int m,
                  const double *__restrict__ Y, const double *__restrict__ theta,
-                 const int *__restrict__ sel, int ks, double *__restrict__ X,
+                 const int *__restrict__ selq, int ks, int j0, double *__restrict__ X,
                  double *__restrict__ R, int64_t n, double *__restrict__ partial) {
     __shared__ double red[32];
-    for (int j0 = 0; j0 < ks; j0 += 8) {
-        const int jn = min(8, ks - j0);
-        double ss[8];
+    double ss[JN];
 #pragma unroll
-        for (int q = 0; q < 8; q++) ss[q] = 0.0;
-        const int *sq = sel + j0;
-        switch (jn) {  // uniform across the grid
-            case 1: ritz_group<1>(V, W, ld, m, Y, theta, sq, X, R, n, ss); break;
-            case 2: ritz_group<2>(V, W, ld, m, Y, theta, sq, X, R, n, ss); break;
-            case 3: ritz_group<3>(V, W, ld, m, Y, theta, sq, X, R, n, ss); break;
-            case 4: ritz_group<4>(V, W, ld, m, Y, theta, sq, X, R, n, ss); break;
-            case 5: ritz_group<5>(V, W, ld, m, Y, theta, sq, X, R, n, ss); break;
-            case 6: ritz_group<6>(V, W, ld, m, Y, theta, sq, X, R, n, ss); break;
-            case 7: ritz_group<7>(V, W, ld, m, Y, theta, sq, X, R, n, ss); break;
-            default: ritz_group<8>(V, W, ld, m, Y, theta, sq, X, R, n, ss); break;
-        }
+    for (int q = 0; q < JN; q++) ss[q] = 0.0;
+    ritz_group<JN>(V, W, ld, m, Y, theta, selq, X, R, n, ss);
 #pragma unroll
-        for (int q = 0; q < 8; q++) {
-            if (q < jn) {  // uniform across the block
-                const double t = block_sum(ss[q], red);
-                if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * ks + j0 + q] = t;
-            }
-        }
+    for (int q = 0; q < JN; q++) {
+        const double t = block_sum(ss[q], red);
+        if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * ks + j0 + q] = t;
     }
 }
 
@@ -381,9 +369,25 @@ int launch_ritz_block(sqd_ctx *ctx, const double *V, const double *W, int64_t ld
                       const double *Y, const double *theta, const int *sel, int ks, double *X,
                       double *R, int64_t n, double *partial, int nblk, double *rnorm2) {
     if (ks == 0 || n == 0) return SQD_OK;
-    k_ritz_block<<<nblk, RED_THREADS, 0, ctx->stream>>>(V, W, ld, m, Y, theta, sel, ks, X, R, n,
-                                                        partial);
-    SQD_LAUNCHED(ctx);
+    for (int j0 = 0; j0 < ks; j0 += 8) {  // one kernel per group of 8 roots
+        const int *sq = sel + j0;
+        cudaStream_t st = ctx->stream;
+        switch (min(8, ks - j0)) {
+#define RITZ_CASE(J)                                                                          \
+    case J:                                                                                   \
+        k_ritz_block<J><<<nblk, RED_THREADS, 0, st>>>(V, W, ld, m, Y, theta, sq, ks, j0, X, R, \
+                                                       n, partial);                           \
+        break;
+            RITZ_CASE(1) RITZ_CASE(2) RITZ_CASE(3) RITZ_CASE(4) RITZ_CASE(5) RITZ_CASE(6)
+            RITZ_CASE(7)
+            default:
+                k_ritz_block<8><<<nblk, RED_THREADS, 0, st>>>(V, W, ld, m, Y, theta, sq, ks, j0,
+                                                              X, R, n, partial);
+                break;
+#undef RITZ_CASE
+        }
+        SQD_LAUNCHED(ctx);
+    }
     k_ritz_final<<<(ks + 63) / 64, 64, 0, ctx->stream>>>(partial, nblk, ks, rnorm2);
     SQD_LAUNCHED(ctx);
     return SQD_OK;
