@@ -1,8 +1,13 @@
-// Device kernels of the Davidson driver: block dot products, basis updates,
-// residuals, the diagonal preconditioner, guess selection, sign fixing and a
-// one-block parallel (round-robin) Jacobi eigensolver for the small
-// Rayleigh-Ritz matrix.  All arithmetic is FP64; reductions run in a fixed
-// order so results do not depend on scheduling.
+// Device kernels of the Davidson driver: block dot products of the new block
+// with the basis (shared-memory tiles, every vector element read from HBM
+// once), basis combinations and block Gram-Schmidt updates (one kernel per
+// output-group width), Ritz vectors with residuals and their norms in one
+// pass, the diagonal (Davidson) and Olsen corrections, the projected matrix
+// Z^T G Z at restart, guess selection, sign fixing and a one-block parallel
+// (round-robin) Jacobi eigensolver for the small Rayleigh-Ritz matrix,
+// optionally warm-started from the previous eigenvectors.  All arithmetic
+// is FP64; reductions run in a fixed order so results do not depend on
+// scheduling.
 #include <cmath>
 
 #include "davidson_body.cuh"
