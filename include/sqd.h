@@ -277,14 +277,19 @@ typedef struct {
  * H_II) with |denominator| clamped to precond_floor (correction = 1: Olsen's
  * modification, t = (r - eps x) / (theta - H_II) with eps chosen so that
  * x^T t = 0, J. Olsen, P. Jorgensen, J. Simons, Chem. Phys. Lett. 169, 463
- * (1990); not in the paper, off by default); classical Gram-Schmidt
- * twice, a vector is dropped if its norm after that is below 1e-12; at the
- * subspace limit the basis restarts from the 2*nroots lowest Ritz vectors
- * plus the nroots Ritz vectors of the previous iteration orthonormalised
- * against them (GD+k restart; max_subspace must be >= 4*nroots);
- * converged when every root has ||r|| <= tol_residual and
- * |delta theta| <= tol_energy.  Rayleigh-Ritz uses a one-block Jacobi
- * eigensolver in FP64.
+ * (1990); not in the paper, off by default).  The corrections of the
+ * unconverged roots form one block, orthogonalised by classical
+ * Gram-Schmidt against the basis (a second pass when a vector lost more
+ * than half its squared norm) and then twice within the block; a vector is
+ * dropped if its norm after that is below 1e-12.  At the subspace limit the
+ * basis restarts from the 2*nroots lowest Ritz vectors plus the nroots Ritz
+ * vectors of the previous iteration orthonormalised against them (GD+k
+ * restart; max_subspace must be >= 4*nroots).  Converged when every root
+ * has ||r|| <= tol_residual and |delta theta| <= tol_energy (delta over the
+ * last growth of the basis) in one iteration; a root that passed is not
+ * re-formed until every root has passed.  Rayleigh-Ritz uses a one-block
+ * Jacobi eigensolver in FP64, started from the previous eigenvectors while
+ * the basis only grows.
  *
  * Outputs: h_energies[nroots] (host), d_C [nroots][n_alpha][n_beta] the
  * Ritz vectors (device, normalised, largest-magnitude component positive),
