@@ -257,7 +257,7 @@ int sqd_sigma_stored(sqd_ctx *ctx, sqd_tables *tables, const double *d_C, double
 typedef struct {
     int nroots;          /* number of lowest eigenpairs (>= 1)                 */
     int max_iter;        /* iteration limit (e.g. 200)                         */
-    int max_subspace;    /* basis size limit; 0 = max(8*nroots, 16)            */
+    int max_subspace;    /* basis size limit; 0 = max(6*nroots, 16)            */
     double tol_energy;   /* |theta - theta_previous| per root                  */
     double tol_residual; /* ||H x - theta x||_2 per root                       */
     double precond_floor;/* clamp of |theta - H_II| (e.g. 1e-8)                */

@@ -360,7 +360,7 @@ def davidson(matvec, hdiag, nroots=1, tol_residual=1e-8, tol_energy=1e-8,
       D the same clamped denominator, so that x^T t = 0;
     * classical Gram-Schmidt applied twice; a vector whose norm after the
       two passes is below ``drop_tol`` is dropped;
-    * subspace limit max(8 * nroots, 16); on reaching it, restart from the
+    * subspace limit max(6 * nroots, 16); on reaching it, restart from the
       2 * nroots lowest Ritz vectors plus the nroots Ritz vectors of the
       previous iteration, orthonormalised against them (the GD+k restart of
       Stathopoulos and Saad, 1998); a previous direction whose norm after
@@ -371,7 +371,7 @@ def davidson(matvec, hdiag, nroots=1, tol_residual=1e-8, tol_energy=1e-8,
     """
     N = len(hdiag)
     if max_subspace is None:
-        max_subspace = max(8 * nroots, 16)
+        max_subspace = max(6 * nroots, 16)
     max_subspace = min(max_subspace, N)
     if guess is None:
         order = np.argsort(hdiag, kind="stable")[:nroots]

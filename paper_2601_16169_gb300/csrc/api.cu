@@ -618,7 +618,7 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
     cudaStream_t st = ctx->stream;
     const int64_t N = t->a.n * t->b->n;
     const int k = o->nroots;
-    int M = o->max_subspace > 0 ? o->max_subspace : std::max(8 * k, 16);
+    int M = o->max_subspace > 0 ? o->max_subspace : std::max(6 * k, 16);
     if (M > 112) M = 112;
     if ((int64_t)M > N) M = (int)N;
     if (M < std::min<int64_t>(4 * k, N))
