@@ -15,11 +15,19 @@ Plain and slow on purpose.  Every function states the passage of arXiv
 * ``dense_h`` + ``eigh``: full diagonalisation of P H P for tiny cases;
 * ``sigma``: matrix-free sigma = (P H P) C recomputing every H_IJ
   (Section II, method 1);
-* ``davidson``: the Davidson eigensolver (Section I, Davidson 1975) with the
-  readings listed in its docstring;
+* ``davidson`` and ``correction_vector``: the Davidson eigensolver
+  (Section I, Davidson 1975) with the readings listed in its docstring, and
+  the correction of one root (Davidson's, or Olsen's as an option);
 * ``rdm1`` / ``rdm2`` / ``orbital_gradient``: the reduced density matrices
   of the converged state and the derivatives of E they give (not in the
-  paper; the Hellmann-Feynman adjoint of the subspace energy).
+  paper; the Hellmann-Feynman adjoint of the subspace energy);
+* ``string_weights`` / ``select_strings`` / ``map_vector``: the carry-over of
+  configurations between SQD rounds (Section I; weights, selection by
+  threshold, warm-start vector on the new sets).
+
+Every function is pinned by ``tests/test_oracle_pins.py`` against something
+other than itself (Jordan-Wigner operator sums, LAPACK, closed forms,
+invariants, finite differences); ``tests/golden/`` holds values it wrote.
 
 Conventions: strings are uint64 (bit k = spatial orbital k); determinant
 index I = ia * nb + ib; a vector C is stored as an na x nb row-major matrix.
@@ -38,7 +46,7 @@ __all__ = [
     "lib", "build_strings", "hij", "dense_h", "sigma", "diag", "excitations",
     "string_energy", "expect", "rdm1", "rdm2", "energy_from_rdms",
     "orbital_gradient", "rotate_integrals", "davidson", "eigh_lowest",
-    "string_weights", "select_strings", "map_vector",
+    "string_weights", "select_strings", "map_vector", "correction_vector",
 ]
 
 _LIB = None
