@@ -473,3 +473,64 @@ def test_outer_loop_helpers_invariants():
     assert len(oracle.select_strings(sa, wa, wa.max() + 1)) == 0
     keep = oracle.select_strings(sa, wa, np.median(wa))
     assert set(keep.tolist()) == {int(x) for x, v in zip(sa, wa) if v >= np.median(wa)}
+
+
+# ------------------------------------------- elementary oracle functions ----
+
+def test_hij_equals_jordan_wigner_elements():
+    # the generic Slater-Condon element of two determinants, against the
+    # Jordan-Wigner operator matrix, with non-symmetric integrals
+    rng = np.random.default_rng(11)
+    norb = 4
+    h, V = _nonsym_integrals(rng, norb)
+    Hf = _jw.hamiltonian(norb, h, V, 0.75)
+    sa, sb = si.full_strings(norb, 2), si.full_strings(norb, 1)
+    for _ in range(60):
+        ia, ja = rng.choice(sa, size=2)
+        ib, jb = rng.choice(sb, size=2)
+        ref = Hf[_jw.fock_index(norb, ia, ib), _jw.fock_index(norb, ja, jb)]
+        got = oracle.hij(norb, h, V, 0.75, ia, ib, ja, jb)
+        assert abs(got - ref) <= 1e-12 * (1.0 + abs(ref))
+
+
+def test_string_energy_equals_one_spin_diagonal():
+    rng = np.random.default_rng(12)
+    norb = 5
+    h, V = _nonsym_integrals(rng, norb)
+    Hf = _jw.hamiltonian(norb, h, V, 0.0, spins=(0,))
+    s = si.full_strings(norb, 3)
+    got = oracle.string_energy(norb, h, V, s)
+    ref = np.array([Hf[_jw.fock_index(norb, x, 0), _jw.fock_index(norb, x, 0)] for x in s])
+    assert np.allclose(got, ref, rtol=1e-13, atol=1e-13)
+
+
+def test_expect_equals_jordan_wigner():
+    # <C| P op P |C> for one- and two-body spin-orbital operator strings
+    rng = np.random.default_rng(13)
+    norb = 3
+    sa, sb = si.full_strings(norb, 2), si.full_strings(norb, 1)
+    C = rng.normal(size=len(sa) * len(sb))
+    dim = 2 ** (2 * norb)
+    idx = [_jw.fock_index(norb, a, b) for a in sa for b in sb]
+    psi = np.zeros(dim)
+    psi[idx] = C
+    P = np.zeros(dim)
+    P[idx] = 1.0
+    ops2 = rng.integers(0, 2 * norb, size=(12, 2))
+    ops4 = rng.integers(0, 2 * norb, size=(12, 4))
+    for ops, kinds in ((ops2, "ca"), (ops4, "ccaa")):
+        got = oracle.expect(norb, sa, sb, C, ops)
+        for row, g in zip(ops, got):
+            op = _jw.operator_matrix(norb, list(zip(kinds, row.tolist())))
+            ref = psi @ (P * (op @ psi))
+            assert abs(g - ref) <= 1e-12 * (1.0 + abs(ref))
+
+
+def test_eigh_lowest_is_the_lowest_eigenpairs():
+    rng = np.random.default_rng(14)
+    A = rng.normal(size=(40, 40))
+    H = A + A.T
+    w, v = oracle.eigh_lowest(H, 3)
+    assert np.allclose(w, np.sort(np.linalg.eigvalsh(H))[:3], rtol=0, atol=1e-11)
+    assert np.allclose(H @ v, v * w, atol=1e-10)
+    assert np.allclose(v.T @ v, np.eye(3), atol=1e-12)
