@@ -58,3 +58,30 @@ def test_no_cpu_fallback():
     import paper_2601_16169_gb300 as sqd
     with pytest.raises(RuntimeError):
         sqd.Context()
+
+
+def test_every_declaration_is_documented():
+    # each declared call is preceded by a comment that cites its passage of
+    # the paper (a Section, Table or Appendix) or says it is not in the paper
+    src = open(os.path.join(ROOT, "include", "sqd.h")).read()
+    pieces = re.split(r"(/\*.*?\*/)", src, flags=re.S)
+    last_comment = ""
+    seen = {}
+    for piece in pieces:
+        if piece.startswith("/*"):
+            last_comment += piece
+            continue
+        for name in re.findall(r"\b(sqd_[a-z_0-9]+)\s*\(", piece):
+            seen.setdefault(name, last_comment)
+        if re.search(r"\b(sqd_[a-z_0-9]+)\s*\(", piece):
+            last_comment = ""
+    assert sorted(seen) == declared_symbols()
+    cites = re.compile(r"Section|Table|App\.|Appendix|not in the paper|paper has no|"
+                       r"no counterpart|\(not in\b", re.I)
+    undocumented = [n for n, c in seen.items() if not c.strip()]
+    assert not undocumented, undocumented
+    uncited = [n for n, c in seen.items() if not cites.search(c)]
+    # calls grouped under one comment share its citation; a group comment
+    # without one must be a housekeeping call (context, errors, version)
+    housekeeping = {"sqd_set_stream", "sqd_last_error", "sqd_version"}
+    assert set(uncited) <= housekeeping, sorted(set(uncited) - housekeeping)
