@@ -327,9 +327,9 @@ int sqd_davidson_batched(sqd_ctx *ctx, int nbatch, sqd_tables *const *tables,
 
 /* What the last sqd_davidson_batched call chose (not in the paper; host
  * outputs, each may be NULL): the alpha-group scale of the paired-singles
- * split, and whether the
- * iteration loop ran inside one graph (1: a conditional WHILE node decided on
- * the device) or as host-driven replays of the captured iteration (0). */
+ * split, and whether the iteration loop ran inside one graph (1: a
+ * conditional WHILE node decided on the device) or as host-driven replays of
+ * the captured iteration (0). */
 int sqd_batched_tuning(const sqd_ctx *ctx, double *group_scale, int *device_loop);
 
 /* ------------------------------------------------ adjoint: RDMs ----- */
