@@ -98,6 +98,8 @@ def _args(argv=None):
                    help="rows of sigma in the CPU-baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--nbatch", type=int, default=64)
+    p.add_argument("--tol-residual", type=float, default=1e-6,
+                   help="batched mode: residual tolerance of both solvers")
     p.add_argument("--sigma-mode", type=int, default=0, choices=[0, 1],
                    help="0: native FP64 sigma (headline); 1: double-float on the FP32 pipe")
     p.add_argument("--correction", default="davidson", choices=["davidson", "olsen"],
@@ -105,6 +107,8 @@ def _args(argv=None):
     p.add_argument("--max-iter", type=int, default=None,
                    help="stop Davidson after this many iterations (short profiling runs; "
                         "the line then reports an unconverged solve)")
+    p.add_argument("--nroots", type=int, default=None,
+                   help="solve mode: number of roots (default: the workload's)")
     p.add_argument("--max-subspace", type=int, default=None,
                    help="Davidson subspace limit (default max(6 nroots, 16))")
     p.add_argument("--stored", action="store_true",
@@ -394,7 +398,11 @@ def sigma_roofline(prof, workload):
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(dom, workload),
             "peak_source": "derived FP64: 152 SMs x 2070 MHz x 4 flop/clk/SM (of derived; "
                            "the FMA-chain probe in fp64_measured is its measured check)",
-            "launch_ms": d["ms"] / d["regions"], "flops_per_launch": d["flops"] / d["regions"]}
+            "launch_ms": d["ms"] / d["regions"], "flops_per_launch": d["flops"] / d["regions"],
+            "compulsory_bytes_per_launch": d["bytes"] / d["regions"],
+            "traffic_note": "DRAM bytes per launch from one ncu capture of this kernel on this "
+                            "workload (profiles/traffic_<workload>.txt); FP64-bound, so DRAM "
+                            "runs at a few percent of its bandwidth whatever the re-reads"}
 
 
 def sigma_summary(prof):
@@ -611,6 +619,8 @@ def run_solve(args, rank, world, local_rank, steps=None, warmup=None, e2e_steps=
     warmup = args.warmup if warmup is None else warmup
     w = si.workload(args.workload)
     opts = dict(SOLVE[args.workload])
+    if getattr(args, "nroots", None):
+        opts["nroots"] = args.nroots
     if args.max_subspace:
         opts["max_subspace"] = args.max_subspace
     if args.max_iter is not None:
@@ -762,7 +772,8 @@ def run_batched(args, rank, world, local_rank, with_cpu=True):
     h = env.tensor(subs[0].h)
     V = env.tensor(subs[0].V)
     raws = [env.tensor(w.raw_a.view(np.int64)) for w in subs]
-    opts = dict(tol_residual=1e-6, tol_energy=1e-8, max_iter=300)
+    tol_r = getattr(args, "tol_residual", 1e-6)
+    opts = dict(tol_residual=tol_r, tol_energy=1e-8, max_iter=400)
 
     def tables():
         return [env.tables(w, r, h, V) for w, r in zip(subs, raws)]
@@ -791,6 +802,7 @@ def run_batched(args, rank, world, local_rank, with_cpu=True):
     launches = ctx.launch_count()
     ctx.profile(False)
     scale, device_loop = sqd.batched_tuning(ctx, with_loop=True)
+    buckets = sqd.batched_tuning_buckets(ctx)
     # the same work as one solve per subspace
     env.sync()
     ev0.record(env.stream)
@@ -813,22 +825,47 @@ def run_batched(args, rank, world, local_rank, with_cpu=True):
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
            "higher_is_better": True, "dtype": "f64",
            "config": {"workload": "%d subspaces, norb=29, 5+5 electrons, 200-3000 strings each "
-                                  "(%.3g determinants in total), ground states, ||r|| <= 1e-6, "
+                                  "(%.3g determinants in total), ground states, ||r|| <= %g, "
                                   "|dE| <= 1e-8; step = tables + batched solve"
-                                  % (len(subs), float(np.sum(ndet)))},
+                                  % (len(subs), float(np.sum(ndet)), tol_r)},
            "sequential_ms": ms_s, "speedup_vs_sequential": ms_s / ms_b,
            "max_abs_energy_diff_vs_sequential": float(np.max(np.abs(np.asarray(e_b) - e_s))),
            "iterations_batched_max": int(np.max(it_b)), "iterations_sequential_max": int(max(it_s)),
            "iterations_batched_sum": int(np.sum(it_b)), "iterations_sequential_sum": int(sum(it_s)),
-           "autotuned_group_scale": scale, "det_total": float(np.sum(ndet)),
+           "max_rel_energy_diff_vs_sequential":
+               float(np.max(np.abs(np.asarray(e_b) - e_s) / np.abs(e_s))),
+           "autotuned_group_scale": scale, "autotuned_buckets": buckets,
+           "det_total": float(np.sum(ndet)),
            "loop_in_one_graph": device_loop,
            "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items() if v["ms"]},
-           "classes": class_record(prof, [k for k in ("batched_sigma", "batched_vector",
-                                                      "batched_eigh") if k in prof]),
+           "classes": class_record(prof, [k for k in ("batched", "batched_sigma",
+                                                      "batched_vector", "batched_eigh")
+                                          if k in prof]),
+           "roofline": batched_roofline(prof),
            "clocks": clocks, "gpu_launches": launches}
     if with_cpu and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_batched(subs, it_b)
     return out
+
+
+def batched_roofline(prof):
+    """The batched loop against its two roofs: the sigma stage's algorithmic
+    flops over its device-timed stage time against the FP64 peak, the vector
+    stages' algorithmic bytes against the HBM copy bandwidth, and the loop
+    as a whole: (sigma flops / FP64 peak + vector bytes / HBM) over the time
+    of the three stages."""
+    if "batched_sigma" not in prof or not prof["batched_sigma"]["ms"]:
+        return None
+    sg, vc, eg = prof["batched_sigma"], prof["batched_vector"], prof["batched_eigh"]
+    t_roof = sg["flops"] / (FP64_PEAK_TFLOPS * 1e12) + vc["bytes"] / (_hbm_peak() * 1e9)
+    t_loop = (sg["ms"] + vc["ms"] + eg["ms"]) / 1e3
+    return {"sigma_frac_fp64": sg["flops"] / (sg["ms"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+            "vector_frac_hbm": vc["bytes"] / (vc["ms"] / 1e3) / 1e9 / _hbm_peak()
+            if vc["ms"] else None,
+            "loop_frac": t_roof / t_loop if t_loop else None,
+            "loop_ms": t_loop * 1e3, "eigh_ms": eg["ms"],
+            "note": "sigma of measured-derived FP64 peak; vector of measured HBM copy "
+                    "bandwidth; loop = roof time / stage time"}
 
 
 def run_adjoint(args, rank, world, local_rank, with_cpu=True):
@@ -897,7 +934,7 @@ def run_adjoint(args, rank, world, local_rank, with_cpu=True):
 def _sub_args(args, **kw):
     a = argparse.Namespace(**vars(args))
     a.sigma_mode, a.stored, a.max_iter, a.max_subspace = 0, False, None, None
-    a.correction, a.cpu_rows, a.e2e_steps = "davidson", None, None
+    a.correction, a.cpu_rows, a.e2e_steps, a.nroots = "davidson", None, None, None
     for k, v in kw.items():
         setattr(a, k, v)
     return a

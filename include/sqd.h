@@ -255,9 +255,10 @@ int sqd_sigma_stored(sqd_ctx *ctx, sqd_tables *tables, const double *d_C, double
 /* ---------------------------------------------------- a8: Davidson -- */
 
 typedef struct {
-    int nroots;          /* number of lowest eigenpairs (>= 1)                 */
+    int nroots;          /* number of lowest eigenpairs, 1..28                 */
     int max_iter;        /* iteration limit (e.g. 200)                         */
-    int max_subspace;    /* basis size limit; 0 = max(6*nroots, 16)            */
+    int max_subspace;    /* basis size limit; 0 = max(6*nroots, 16); values    */
+                         /*    above 112 (the eigensolver's limit) are capped  */
     double tol_energy;   /* |theta - theta_previous| per root                  */
     double tol_residual; /* ||H x - theta x||_2 per root                       */
     double precond_floor;/* clamp of |theta - H_II| (e.g. 1e-8)                */
@@ -280,8 +281,16 @@ typedef struct {
  * (1990); not in the paper, off by default).  The corrections of the
  * unconverged roots form one block, orthogonalised by classical
  * Gram-Schmidt against the basis (a second pass when a vector lost more
- * than half its squared norm) and then twice within the block; a vector is
- * dropped if its norm after that is below 1e-12.  At the subspace limit the
+ * than half its squared norm, decided on the device) and then twice within
+ * the block (from the block's Gram matrix, Cholesky QR twice, where every
+ * vector keeps 1e-8 of its squared norm; vector by vector otherwise); a
+ * vector is dropped if its norm after that is below 1e-12.  With
+ * one root (and the Davidson correction, max_subspace <= 16) the passes are
+ * fused and both run: the correction and its first projections come from
+ * the pass that forms the Ritz pair, and the norm after the second pass
+ * follows from Pythagoras, |t''|^2 = |t'|^2 - |V^T t'|^2, unless that
+ * difference is not safely resolved (then it is taken explicitly).  At the
+ * subspace limit the
  * basis restarts from the 2*nroots lowest Ritz vectors plus the nroots Ritz
  * vectors of the previous iteration orthonormalised against them (GD+k
  * restart; max_subspace must be >= 4*nroots).  Converged when every root
@@ -296,7 +305,8 @@ typedef struct {
  * *h_iters (host, may be NULL), h_residuals[nroots] (host, may be NULL).
  * Returns SQD_ENOTCONVERGED (with the last estimates written) when max_iter
  * is reached, SQD_EBREAKDOWN if no new direction survives orthogonalisation
- * before convergence.
+ * (or the basis spans the whole space) before convergence, SQD_EINVAL for
+ * nroots outside [1, min(28, dimension)] or max_subspace < 4*nroots.
  */
 int sqd_davidson(sqd_ctx *ctx, sqd_tables *tables, const sqd_options *opt,
                  double *h_energies, double *d_C, int *h_iters,
@@ -309,11 +319,16 @@ int sqd_davidson(sqd_ctx *ctx, sqd_tables *tables, const sqd_options *opt,
  * subsampled configuration sets per round, Section I; each is one table
  * object from sqd_excitation_tables, all on this context's device).
  * Same Davidson readings as sqd_davidson with nroots == 1 (required),
- * max_subspace 0 meaning 16.  Every step runs as one launch over all
+ * max_subspace 0 meaning 16 (larger values are capped at 16), and the same
+ * fused one-vector passes.  Every step runs as one launch over all
  * subspaces; one iteration is captured in a CUDA graph and replayed until
- * every subspace has converged or stopped.  The number of alpha-row groups
- * of the paired-singles work per subspace is autotuned at the start by
- * timing candidate values on the first sigma.
+ * every subspace has converged or stopped.  The paired-singles tile is
+ * autotuned at the start per size bucket (up to 4 buckets of equal count by
+ * determinant count): for each bucket, the kernel variant (16 entries per
+ * thread over 4096-entry chunks in a persistent work-queue kernel, or 8
+ * entries per thread over 2048-entry chunks in a grid) and the alpha-row
+ * group count (0.5, 1 or 2 times the table's default split) are timed on
+ * the first sigma of up to 4 of the bucket's largest subspaces.
  *
  * h_energies[nbatch] (host), d_C[b] (device, n_alpha*n_beta doubles each,
  * may be NULL to skip the vector; normalised, largest component positive),
@@ -331,6 +346,22 @@ int sqd_davidson_batched(sqd_ctx *ctx, int nbatch, sqd_tables *const *tables,
  * conditional WHILE node decided on the device) or as host-driven replays of
  * the captured iteration (0). */
 int sqd_batched_tuning(const sqd_ctx *ctx, double *group_scale, int *device_loop);
+
+/* Fix the paired-singles tile of later sqd_davidson_batched calls on this
+ * context instead of autotuning it (not in the paper; for tests and
+ * measurements): entries_per_thread 16 (persistent kernel, wide chunks) or 8
+ * (grid kernel, standard chunks) with group_scale 0.5, 1 or 2;
+ * entries_per_thread 0 restores autotuning.  Errors: SQD_EINVAL. */
+int sqd_batched_set_tile(sqd_ctx *ctx, int entries_per_thread, double group_scale);
+
+/* The per-bucket tiles of the last sqd_davidson_batched call (not in the
+ * paper): *nbuckets (host) receives the bucket count; for the first
+ * min(*nbuckets, max_buckets) buckets, in increasing size, h_max_det[q] the
+ * largest subspace of the bucket (determinants), h_scale[q] its alpha-group
+ * scale and h_entries[q] its entries per thread (16: persistent, 8: grid).
+ * Each array may be NULL. */
+int sqd_batched_tuning_buckets(const sqd_ctx *ctx, int max_buckets, int *nbuckets,
+                               int64_t *h_max_det, double *h_scale, int *h_entries);
 
 /* ------------------------------------------------ adjoint: RDMs ----- */
 
@@ -369,7 +400,11 @@ int sqd_orbital_gradient(sqd_ctx *ctx, sqd_tables *tables, const double *d_rdm1,
  *   4 tables, 5 strings, 6 davidson (Ritz vectors, residuals,
  *   preconditioner, restart), 7 rdm, 8 stored, 9 ortho (Davidson
  *   Gram-Schmidt and projected-matrix columns), 10 eigh (Rayleigh-Ritz
- *   eigensolver).
+ *   eigensolver), 11 batched (a whole sqd_davidson_batched call),
+ *   12 batched_sigma, 13 batched_vector, 14 batched_eigh (the stages of the
+ *   batched iteration loop: timed on the device with the global timer at the
+ *   stage boundaries inside the captured loop, one region per iteration;
+ *   flops and bytes summed over the subspaces each stage served).
  * sqd_profile_read returns, for one class, the class name (static string),
  * the number of regions, their summed event time in ms, and the
  * algorithmic FP64 flops and compulsory bytes booked for them (host

@@ -48,12 +48,14 @@ EXPORTED = [
     "sqd_tables_export", "sqd_diagonal", "sqd_sigma", "sqd_davidson", "sqd_rdm",
     "sqd_profile_enable", "sqd_profile_read", "sqd_launch_count", "sqd_orbital_gradient",
     "sqd_build_strings_noalloc", "sqd_davidson_batched", "sqd_batched_tuning",
+    "sqd_batched_tuning_buckets", "sqd_batched_set_tile",
     "sqd_stored_h_build", "sqd_sigma_stored", "sqd_string_weights", "sqd_select_strings",
     "sqd_map_vector", "sqd_tables_set_sigma_mode", "sqd_measure_fp64_peaks",
 ]
 
 PROFILE_CLASSES = ["same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose", "tables",
-                   "strings", "davidson", "rdm", "stored", "ortho", "eigh"]
+                   "strings", "davidson", "rdm", "stored", "ortho", "eigh", "batched",
+                   "batched_sigma", "batched_vector", "batched_eigh"]
 
 
 class SQDError(RuntimeError):
@@ -114,6 +116,8 @@ def lib():
     L.sqd_build_strings_noalloc.argtypes = [vp, vp, i64, i32, i32, vp, ctypes.POINTER(i64)]
     L.sqd_davidson_batched.argtypes = [vp, i32, vp, ctypes.POINTER(Options), vp, vp, vp, vp]
     L.sqd_batched_tuning.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
+    L.sqd_batched_tuning_buckets.argtypes = [vp, i32, ctypes.POINTER(i32), vp, vp, vp]
+    L.sqd_batched_set_tile.argtypes = [vp, i32, dbl]
     L.sqd_stored_h_build.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
     L.sqd_sigma_stored.argtypes = [vp, vp, vp, vp, i32]
     L.sqd_string_weights.argtypes = [vp, vp, vp, vp, vp]
@@ -454,6 +458,30 @@ def batched_tuning(ctx: Context, with_loop: bool = False):
     dl = ctypes.c_int()
     ctx._check(ctx._lib.sqd_batched_tuning(ctx.handle, ctypes.byref(v), ctypes.byref(dl)))
     return (v.value, bool(dl.value)) if with_loop else v.value
+
+
+def batched_set_tile(ctx: Context, entries_per_thread: int = 0, group_scale: float = 1.0):
+    """sqd_batched_set_tile: fix the paired-singles tile of later batched
+    solves (16 or 8 entries per thread, group scale 0.5 / 1 / 2); 0 restores
+    autotuning."""
+    ctx._check(ctx._lib.sqd_batched_set_tile(ctx.handle, int(entries_per_thread),
+                                             float(group_scale)))
+
+
+def batched_tuning_buckets(ctx: Context):
+    """sqd_batched_tuning_buckets: the paired-singles tile chosen per size
+    bucket by the last batched solve, as a list of dicts (max_det, scale,
+    entries_per_thread) in increasing bucket size."""
+    import numpy as np
+    n = ctypes.c_int(0)
+    md = np.zeros(16, dtype=np.int64)
+    sc = np.zeros(16)
+    ep = np.zeros(16, dtype=np.int32)
+    ctx._check(ctx._lib.sqd_batched_tuning_buckets(
+        ctx.handle, 16, ctypes.byref(n), ctypes.c_void_p(md.ctypes.data),
+        ctypes.c_void_p(sc.ctypes.data), ctypes.c_void_p(ep.ctypes.data)))
+    return [dict(max_det=int(md[q]), scale=float(sc[q]), entries_per_thread=int(ep[q]))
+            for q in range(min(n.value, 16))]
 
 
 def rdm(ctx: Context, tables: Tables, C: torch.Tensor, two_body: bool = True):

@@ -1,5 +1,6 @@
 // C ABI of the SQD library (include/sqd.h): context, validation, string
 // filtering, table construction, sigma, Davidson and RDM orchestration.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -147,7 +148,8 @@ void sqd_destroy(sqd_ctx *ctx) {
 static const char *k_prof_names[PROF_NCLASS] = {
     "same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose",
     "tables",          "strings",        "davidson",   "rdm", "stored",
-    "ortho",           "eigh"};
+    "ortho",           "eigh",           "batched",    "batched_sigma", "batched_vector",
+    "batched_eigh"};
 
 int sqd_profile_enable(sqd_ctx *ctx, int enable) {
     if (!ctx) return fail_noctx(SQD_EINVAL, "sqd_profile_enable: ctx is NULL");
@@ -522,7 +524,7 @@ static int ensure_scratch(sqd_ctx *ctx, sqd_tables *t) {
 //  beta side : na*(2*nnz1_b + nnz2_b)
 //  alpha-beta: nnz1_a * nnz1_b
 // and their compulsory HBM bytes (read C, read/write sigma, the diagonal).
-static void sigma_work(const sqd_tables *t, double *f_a, double *f_b, double *f_ab) {
+extern "C++" void sigma_work(const sqd_tables *t, double *f_a, double *f_b, double *f_ab) {
     const double na = (double)t->a.n, nb = (double)t->b->n;
     *f_a = 2.0 * (na * nb + nb * (2.0 * t->a.nnz1 + t->a.nnz2));
     *f_b = 2.0 * na * (2.0 * t->b->nnz1 + t->b->nnz2);
@@ -601,17 +603,29 @@ struct dav_work {
 // projected matrix G = V^T H V (one-block Jacobi), Ritz vectors and residuals
 // of the nroots lowest pairs in one pass over V and W, convergence test, the
 // preconditioned residuals of the unconverged roots as one new block,
-// Gram-Schmidt of that block against V (block classical Gram-Schmidt, second
-// pass by the Daniel-Gragg-Kaufman-Stewart test), then within the block (CGS
-// twice per vector, dropping vectors below 1e-12), H applied to the block and
-// the new columns of G.  In exact arithmetic this is the same basis as
-// vector-by-vector CGS2 of the preconditioned residuals in root order.
-// Second Gram-Schmidt pass of a new block when some vector lost more than
-// this fraction of its squared norm in the first (Daniel-Gragg-Kaufman-
-// Stewart test with eta^2 = 1 - SQD_REORTH_LOSS).
+// Gram-Schmidt of that block against V (block classical Gram-Schmidt, two
+// passes when the first lost more than half a vector's squared norm), then
+// within the block (CGS twice per vector, dropping vectors below 1e-12; from
+// the block's Gram matrix where that is resolved), H applied to the block and
+// the new columns of G.  In exact
+// arithmetic this is the same basis as vector-by-vector CGS2 of the
+// preconditioned residuals in root order.
+//
+// Second block Gram-Schmidt pass when a vector lost more than this fraction
+// of its squared norm in the first (Daniel-Gragg-Kaufman-Stewart test with
+// eta^2 = 1 - SQD_REORTH_LOSS), decided on the device.
 #ifndef SQD_REORTH_LOSS
 #define SQD_REORTH_LOSS 0.5
 #endif
+
+// One root (block width one, m <= 16, Davidson correction): the fused passes
+// of k_davidson.cu form the correction and its first projections in the pass
+// that reads V and W for the Ritz pair (the Ritz vector is formed only on
+// exit), fuse the first update with the second projections, and the second
+// update with the normalisation, whose norm follows from Pythagoras
+// (|t''|^2 = |t'|^2 - |V^T t'|^2 for orthonormal V).  Where that difference
+// is not safely resolved (the second pass removed more than half of |t'|^2,
+// or |t''| < 1e-10) the norm is taken explicitly, as in the general path.
 
 static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, double *h_energies,
                          double *d_C, int *h_iters, double *h_res) {
@@ -619,7 +633,7 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
     const int64_t N = t->a.n * t->b->n;
     const int k = o->nroots;
     int M = o->max_subspace > 0 ? o->max_subspace : std::max(6 * k, 16);
-    if (M > 112) M = 112;
+    if (M > SQD_MAX_SUBSPACE) M = SQD_MAX_SUBSPACE;
     if ((int64_t)M > N) M = (int)N;
     if (M < std::min<int64_t>(4 * k, N))
         return sqd_fail(ctx, SQD_EINVAL, "max_subspace must be >= 4*nroots (or the dimension)");
@@ -628,23 +642,26 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
     const int nbr = 4 * ctx->sm_count;
     const int k2 = std::min(2 * k, M);
     const int kr = std::min(3 * k, M);  // restart basis: 2k Ritz + k previous Ritz
+    // one-root fused passes (register-resident projections need m <= MDf)
+    const int MDf = (k == 1 && o->correction == 0) ? fused_md(M) : 0;
     dav_work w;
     // partial sums: multidot (M x nblk), block dot (nbd x M x k), Ritz (nbr x k),
-    // preconditioner with Olsen's dots (2 x nbr + 2)
+    // preconditioner with Olsen's dots (2 x nbr + 2), fused passes (nbr x (MDf + 2))
     const int64_t npart = std::max<int64_t>(
-        std::max<int64_t>((int64_t)M * nblk, (int64_t)nbd * M * k),
-        std::max<int64_t>((int64_t)nbr * std::max(k, 1), 2LL * nbr + 2));
+        std::max<int64_t>(std::max<int64_t>((int64_t)M * nblk, (int64_t)nbd * M * k),
+                          std::max<int64_t>((int64_t)nbr * std::max(k, 1), 2LL * nbr + 2)),
+        (int64_t)nbr * (MDf + 2));
     SQD_TRY(dalloc(ctx, &w.Vb, (int64_t)M * N));
     SQD_TRY(dalloc(ctx, &w.Wb, (int64_t)M * N));
     SQD_TRY(dalloc(ctx, &w.X, (int64_t)k * N));
     SQD_TRY(dalloc(ctx, &w.R, (int64_t)k * N));
-    SQD_TRY(dalloc(ctx, &w.Tmp, (int64_t)kr * N));
+    if (!MDf) SQD_TRY(dalloc(ctx, &w.Tmp, (int64_t)kr * N));
     SQD_TRY(dalloc(ctx, &w.Yprev, (int64_t)M * k));
     SQD_TRY(dalloc(ctx, &w.Z, (int64_t)M * kr));
-    SQD_TRY(dalloc(ctx, &w.P, (int64_t)M * k));
+    SQD_TRY(dalloc(ctx, &w.P, (int64_t)M * k + 3 * (MDf + 2)));
     SQD_TRY(dalloc(ctx, &w.GZ, (int64_t)M * kr));
     SQD_TRY(dalloc(ctx, &w.tn2, k));
-    SQD_TRY(dalloc(ctx, &w.rdev, 1));
+    SQD_TRY(dalloc(ctx, &w.rdev, 2));  // [0] restart size, [1] second-pass gate
     SQD_TRY(dalloc(ctx, &w.sel, k));
     SQD_TRY(dalloc(ctx, &w.G, (int64_t)M * M));
     SQD_TRY(dalloc(ctx, &w.evals, M));
@@ -657,6 +674,8 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
     SQD_TRY(dalloc(ctx, &w.idx, k));
     SQD_TRY(ensure_scratch(ctx, t));
     const double dN = (double)N;
+    // fused-pass sums: s1 = (V^T t, |r|^2, |t|^2), s2 = (V^T t', |t'|^2), s3 = restarted V^T t
+    double *s1 = w.P + (int64_t)M * k, *s2 = s1 + (MDf + 2), *s3 = s2 + (MDf + 2);
 
     // G[0..m, m0..m0+b) = V[0..m)^T W[m0..m0+b)
     auto g_cols = [&](int m, int m0, int b) -> int {
@@ -666,35 +685,12 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
         prof_end(ctx, 2.0 * m * b * dN, 8.0 * (m + b) * dN);
         return SQD_OK;
     };
-    // Orthonormalise the block T = V[m0..m0+b) against V[0..m0) and within
-    // itself; tn2[j] (host) = |T_j|^2 before, or NULL to always take two
-    // passes.  Accepted vectors are packed to V[m0..m0+*nacc).
-    std::vector<double> hP((size_t)M * k), htn2(k);
-    auto orthonormalize_block = [&](int m0, int b, bool have_tn2, int *nacc) -> int {
+    // Within-block Gram-Schmidt of the vectors V[m0..m0+b) (already
+    // orthogonal to V[0..m0)): CGS twice per vector against the accepted
+    // ones, drop below 1e-12, normalise; accepted vectors are packed to
+    // V[m0..m0+*nacc).
+    auto within_block = [&](int m0, int b, int *nacc) -> int {
         double *T = w.Vb + (int64_t)m0 * N;
-        if (m0 > 0) {
-            for (int pass = 0; pass < 2; pass++) {
-                prof_begin(ctx, PROF_ORTHO);
-                SQD_TRY(launch_block_dot(ctx, w.Vb, N, m0, T, N, b, N, w.partial, nbd, w.P, m0));
-                SQD_TRY(launch_combine_sub(ctx, w.Vb, N, m0, w.P, m0, b, T, N, N));
-                prof_end(ctx, 4.0 * m0 * b * dN, 8.0 * (m0 + 2.0 * b) * dN + 8.0 * m0 * dN);
-                if (pass == 1 || !have_tn2) continue;
-                // DGKS: |T_j|^2 after the pass is |T_j|^2 - |P_j|^2 (V orthonormal);
-                // a second pass unless every vector kept half its squared norm
-                SQD_CUDA(ctx, cudaMemcpyAsync(hP.data(), w.P, sizeof(double) * m0 * b,
-                                              cudaMemcpyDeviceToHost, st));
-                SQD_CUDA(ctx, cudaMemcpyAsync(htn2.data(), w.tn2, sizeof(double) * b,
-                                              cudaMemcpyDeviceToHost, st));
-                SQD_CUDA(ctx, cudaStreamSynchronize(st));
-                bool again = false;
-                for (int j = 0; j < b && !again; j++) {
-                    double p2 = 0.0;
-                    for (int i = 0; i < m0; i++) p2 += hP[i + (size_t)j * m0] * hP[i + (size_t)j * m0];
-                    again = !(p2 <= SQD_REORTH_LOSS * htn2[j]);
-                }
-                if (!again) break;
-            }
-        }
         int acc = 0;
         for (int j = 0; j < b; j++) {
             double *dst = T + (int64_t)acc * N;
@@ -717,6 +713,118 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
         }
         *nacc = acc;
         return SQD_OK;
+    };
+    // Within-block Gram-Schmidt of b >= 2 vectors from their Gram matrix
+    // (one block-dot pass instead of a chain of per-vector passes and host
+    // round trips): CGS twice on the b x b Gram matrix in order gives the
+    // coefficients Z (upper triangular) of the same orthonormal vectors,
+    // Q = T Z, which are formed in one pass; a second round on the Gram
+    // matrix of Q removes the rounding the first left (Cholesky QR twice,
+    // Fukaya et al. 2014).  Used only while every vector keeps at least
+    // 1e-8 of its squared norm (|t| > 1e-10 too), where the Gram matrix
+    // resolves the result; otherwise *ok = false and nothing was changed.
+    std::vector<double> hG, hZ;
+    // work of the last gated second pass, booked when its flag is read
+    double pend_f = 0.0, pend_b = 0.0;
+    int gate_h = 0;
+    auto book_gated = [&]() {
+        if (ctx->prof && gate_h && pend_f > 0.0) {
+            ctx->cls_flops[PROF_ORTHO] += pend_f;
+            ctx->cls_bytes[PROF_ORTHO] += pend_b;
+        }
+        pend_f = pend_b = 0.0;
+    };
+    auto within_block_gram = [&](int m0, int b, int *nacc, bool *ok) -> int {
+        double *T = w.Vb + (int64_t)m0 * N;
+        double *Zd = w.GZ;
+        *ok = false;
+        hG.assign((size_t)b * b, 0.0);
+        hZ.assign((size_t)b * b, 0.0);
+        for (int round = 0; round < 2; round++) {
+            prof_begin(ctx, PROF_ORTHO);
+            SQD_TRY(launch_block_dot(ctx, T, N, b, T, N, b, N, w.partial, nbd, w.P, b));
+            prof_end(ctx, 2.0 * b * b * dN, 16.0 * b * dN);
+            SQD_CUDA(ctx, cudaMemcpyAsync(hG.data(), w.P, sizeof(double) * b * b,
+                                          cudaMemcpyDeviceToHost, st));
+            SQD_CUDA(ctx, cudaStreamSynchronize(st));
+            std::fill(hZ.begin(), hZ.end(), 0.0);
+            std::vector<double> z(b), gz(b);
+            for (int j = 0; j < b; j++) {
+                std::fill(z.begin(), z.end(), 0.0);
+                z[j] = 1.0;
+                for (int pass = 0; pass < 2; pass++) {
+                    for (int l = 0; l < b; l++) {  // gz = G z
+                        double a = 0.0;
+                        for (int q = 0; q < b; q++) a += hG[l + (size_t)q * b] * z[q];
+                        gz[l] = a;
+                    }
+                    std::vector<double> c(j, 0.0);
+                    for (int i = 0; i < j; i++)  // c_i = Q_i . (T z) = Z_i^T G z
+                        for (int l = 0; l < b; l++) c[i] += hZ[l + (size_t)i * b] * gz[l];
+                    for (int i = 0; i < j; i++)
+                        for (int l = 0; l < b; l++) z[l] -= c[i] * hZ[l + (size_t)i * b];
+                }
+                double n2 = 0.0;
+                for (int l = 0; l < b; l++) {
+                    double a = 0.0;
+                    for (int q = 0; q < b; q++) a += hG[l + (size_t)q * b] * z[q];
+                    n2 += z[l] * a;
+                }
+                const double d = hG[j + (size_t)j * b];
+                if (!(n2 >= 1e-8 * d) || !(n2 >= 1e-20)) {
+                    if (round == 0) return SQD_OK;  // not resolved: explicit path
+                    return sqd_fail(ctx, SQD_EBREAKDOWN, "block lost orthogonality");
+                }
+                const double inv = 1.0 / std::sqrt(n2);
+                for (int l = 0; l < b; l++) hZ[l + (size_t)j * b] = z[l] * inv;
+            }
+            SQD_CUDA(ctx, cudaMemcpyAsync(Zd, hZ.data(), sizeof(double) * b * b,
+                                          cudaMemcpyHostToDevice, st));
+            prof_begin(ctx, PROF_ORTHO);
+            SQD_TRY(launch_combine(ctx, T, N, b, Zd, b, b, w.Tmp, N, N));
+            SQD_CUDA(ctx, cudaMemcpyAsync(T, w.Tmp, sizeof(double) * b * N,
+                                          cudaMemcpyDeviceToDevice, st));
+            prof_end(ctx, 1.0 * b * (b + 1) * dN, 8.0 * 4.0 * b * dN);
+        }
+        *nacc = b;
+        *ok = true;
+        return SQD_OK;
+    };
+    // Orthonormalise the block T = V[m0..m0+b) against V[0..m0) (block CGS)
+    // and within itself.  The second block pass runs when some vector lost
+    // more than half its squared norm in the first (Daniel-Gragg-Kaufman-
+    // Stewart test), decided on the device: its kernels read the flag and
+    // exit, so no host round trip sits between the passes.  tn2 (device) holds
+    // the squared norms before the first pass; without it both passes run.
+    auto orthonormalize_block = [&](int m0, int b, bool have_tn2, int *nacc) -> int {
+        double *T = w.Vb + (int64_t)m0 * N;
+        if (m0 > 0) {
+            for (int pass = 0; pass < 2; pass++) {
+                const int *gate = (pass == 1 && have_tn2) ? w.rdev + 1 : nullptr;
+                prof_begin(ctx, PROF_ORTHO);
+                SQD_TRY(launch_block_dot(ctx, w.Vb, N, m0, T, N, b, N, w.partial, nbd, w.P, m0,
+                                         gate));
+                if (pass == 0 && have_tn2)
+                    SQD_TRY(launch_dgks_flag(ctx, w.P, m0, m0, b, w.tn2, SQD_REORTH_LOSS,
+                                             w.rdev + 1));
+                SQD_TRY(launch_combine_sub(ctx, w.Vb, N, m0, w.P, m0, b, T, N, N, gate));
+                const double f = 4.0 * m0 * b * dN, by = 8.0 * (m0 + 2.0 * b) * dN + 8.0 * m0 * dN;
+                if (gate) {
+                    // a gated pass is booked once the host learns whether it ran
+                    prof_end(ctx, 0.0, 0.0);
+                    pend_f = f;
+                    pend_b = by;
+                } else {
+                    prof_end(ctx, f, by);
+                }
+            }
+        }
+        if (b >= 2 && w.Tmp && b <= kr) {
+            bool ok = false;
+            SQD_TRY(within_block_gram(m0, b, nacc, &ok));
+            if (ok) return SQD_OK;
+        }
+        return within_block(m0, b, nacc);
     };
 
     int m = 0;
@@ -769,117 +877,248 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
         for (int j = 0; j < k; j++) rn[j] = std::sqrt(std::max(rn2[j], 0.0));
         return SQD_OK;
     };
-    for (;;) {
-        prof_begin(ctx, PROF_EIGH);
-        SQD_TRY(launch_jacobi_eigh(ctx, w.G, M, m, w.evals, w.evecs, m_warm, w.Eold, w.thold));
-        prof_end(ctx, 0.0, 0.0);
-        sel.clear();
-        for (int j = 0; j < k; j++)
-            if (!locked[j]) sel.push_back(j);
-        const bool full = sel.empty();
-        if (full)
-            for (int j = 0; j < k; j++) sel.push_back(j);
-        const int ks = (int)sel.size();
-        SQD_CUDA(ctx, cudaMemcpyAsync(w.sel, sel.data(), sizeof(int) * ks, cudaMemcpyHostToDevice,
-                                      st));
-        prof_begin(ctx, PROF_DAVIDSON);
-        SQD_TRY(launch_ritz_block(ctx, w.Vb, w.Wb, N, m, w.evecs, w.evals, w.sel, ks, w.X, w.R, N,
-                                  w.partial, nbr, w.dots));
-        prof_end(ctx, 4.0 * m * ks * dN + 2.0 * ks * dN, 8.0 * (2.0 * m + 2.0 * ks) * dN);
-        SQD_CUDA(ctx, cudaMemcpyAsync(theta.data(), w.evals, sizeof(double) * m,
-                                      cudaMemcpyDeviceToHost, st));
-        SQD_CUDA(ctx, cudaMemcpyAsync(rn2.data(), w.dots, sizeof(double) * ks,
-                                      cudaMemcpyDeviceToHost, st));
+    // GD+k restart basis Z (m x r) of the current eigensolve; returns r
+    auto restart_basis = [&](int *r) -> int {
+        const int m2 = std::min(k2, m);
+        SQD_TRY(launch_gdk_basis(ctx, w.evecs, m, m2, mprev ? w.Yprev : nullptr, mprev, k, M,
+                                 w.Z, M, w.rdev));
+        *r = m2;
+        SQD_CUDA(ctx, cudaMemcpyAsync(r, w.rdev, sizeof(int), cudaMemcpyDeviceToHost, st));
         SQD_CUDA(ctx, cudaStreamSynchronize(st));
-        if (grown)
-            for (int j = 0; j < k; j++) dth[j] = std::fabs(theta[j] - theta_old[j]);
-        for (int j = 0; j < k; j++) theta_old[j] = theta[j];
-        bool all = true;
-        std::vector<int> todo;
-        for (int q = 0; q < ks; q++) {
-            const int j = sel[q];
-            rn[j] = std::sqrt(std::max(rn2[q], 0.0));
-            const bool c = rn[j] <= o->tol_residual && dth[j] <= o->tol_energy;
-            locked[j] = c ? 1 : 0;
-            if (!c) {
-                all = false;
-                todo.push_back(j);
-            }
-        }
-        if (full && all) break;
-        if (it >= o->max_iter) {
-            status = SQD_ENOTCONVERGED;
-            if (!full) SQD_TRY(ritz_all());
-            break;
-        }
-        it++;
-        grown = !todo.empty();
-        if (todo.empty()) continue;  // every root locked: check them all next
-        if (m + (int)todo.size() > M) {
-            // restart (GD+k): the 2k lowest Ritz vectors plus the k Ritz vectors
-            // of the previous iteration, orthonormalised against them
-            int m2 = std::min(k2, m);
-            SQD_TRY(launch_gdk_basis(ctx, w.evecs, m, m2, mprev ? w.Yprev : nullptr, mprev, k, M,
-                                     w.Z, M, w.rdev));
-            int r = m2;
-            SQD_CUDA(ctx, cudaMemcpyAsync(&r, w.rdev, sizeof(int), cudaMemcpyDeviceToHost, st));
-            SQD_CUDA(ctx, cudaStreamSynchronize(st));
+        return SQD_OK;
+    };
+    // the basis only grew: keep the Ritz coefficients and seed the next eigensolve
+    auto keep_coefficients = [&]() -> int {
+        SQD_CUDA(ctx, cudaMemcpy2DAsync(w.Yprev, sizeof(double) * M, w.evecs, sizeof(double) * m,
+                                        sizeof(double) * m, k, cudaMemcpyDeviceToDevice, st));
+        mprev = m;
+        SQD_CUDA(ctx, cudaMemcpyAsync(w.Eold, w.evecs, sizeof(double) * m * m,
+                                      cudaMemcpyDeviceToDevice, st));
+        SQD_CUDA(ctx, cudaMemcpyAsync(w.thold, w.evals, sizeof(double) * m,
+                                      cudaMemcpyDeviceToDevice, st));
+        m_warm = m;
+        return SQD_OK;
+    };
+
+    if (MDf) {
+        // ------------------------------------------ one root, fused passes --
+        double hs[36];
+        bool x_ready = false;
+        for (;;) {
+            prof_begin(ctx, PROF_EIGH);
+            SQD_TRY(launch_jacobi_eigh(ctx, w.G, M, m, w.evals, w.evecs, m_warm, w.Eold,
+                                       w.thold));
+            prof_end(ctx, 0.0, 0.0);
+            const bool restart = m + 1 > M;
+            double *T = restart ? w.R : w.Vb + (int64_t)m * N;
             prof_begin(ctx, PROF_DAVIDSON);
-            SQD_TRY(launch_combine(ctx, w.Vb, N, m, w.Z, M, r, w.Tmp, N, N));
-            SQD_CUDA(ctx, cudaMemcpyAsync(w.Vb, w.Tmp, sizeof(double) * r * N,
-                                          cudaMemcpyDeviceToDevice, st));
-            SQD_TRY(launch_combine(ctx, w.Wb, N, m, w.Z, M, r, w.Tmp, N, N));
-            SQD_CUDA(ctx, cudaMemcpyAsync(w.Wb, w.Tmp, sizeof(double) * r * N,
-                                          cudaMemcpyDeviceToDevice, st));
-            // projected matrix of the new basis: G' = Z^T G Z
-            SQD_TRY(launch_project_g(ctx, w.G, M, m, w.Z, M, r, w.GZ));
-            prof_end(ctx, 4.0 * m * r * dN, 8.0 * (2.0 * m + 4.0 * r) * dN);
-            m = r;
-            // the current Ritz vectors are the first k basis vectors now
-            SQD_TRY(launch_identity_cols(ctx, w.Yprev, m, k, M));
-            mprev = m;
-            m_warm = 0;
-        } else {
-            SQD_CUDA(ctx, cudaMemcpy2DAsync(w.Yprev, sizeof(double) * M, w.evecs,
-                                            sizeof(double) * m, sizeof(double) * m, k,
-                                            cudaMemcpyDeviceToDevice, st));
-            mprev = m;
-            // this eigensolve seeds the next one (the basis only grows)
-            SQD_CUDA(ctx, cudaMemcpyAsync(w.Eold, w.evecs, sizeof(double) * m * m,
-                                          cudaMemcpyDeviceToDevice, st));
-            SQD_CUDA(ctx, cudaMemcpyAsync(w.thold, w.evals, sizeof(double) * m,
-                                          cudaMemcpyDeviceToDevice, st));
-            m_warm = m;
+            SQD_TRY(launch_ritz_prec_dot(ctx, MDf, w.Vb, w.Wb, N, m, w.evecs, w.evals, t->diag,
+                                         o->precond_floor, N, T, w.partial, nbr, s1));
+            prof_end(ctx, (6.0 * m + 7.0) * dN, 8.0 * (2.0 * m + 3.0) * dN);
+            SQD_CUDA(ctx, cudaMemcpyAsync(hs, s1 + m, sizeof(double) * 2, cudaMemcpyDeviceToHost,
+                                          st));
+            SQD_CUDA(ctx, cudaMemcpyAsync(theta.data(), w.evals, sizeof(double),
+                                          cudaMemcpyDeviceToHost, st));
+            SQD_CUDA(ctx, cudaStreamSynchronize(st));
+            if (grown) dth[0] = std::fabs(theta[0] - theta_old[0]);
+            theta_old[0] = theta[0];
+            rn[0] = std::sqrt(std::max(hs[0], 0.0));
+            if (rn[0] <= o->tol_residual && dth[0] <= o->tol_energy) break;
+            if (it >= o->max_iter) {
+                status = SQD_ENOTCONVERGED;
+                break;
+            }
+            it++;
+            const double *P1 = s1;
+            if (restart && (int64_t)m >= N) {
+                // the basis spans the whole space: the Ritz pair is exact
+                if (!(rn[0] <= o->tol_residual)) status = SQD_EBREAKDOWN;
+                break;
+            }
+            if (restart) {
+                int r = 0;
+                SQD_TRY(restart_basis(&r));
+                if (r >= M) return sqd_fail(ctx, SQD_EINVAL, "restart basis fills the subspace");
+                prof_begin(ctx, PROF_DAVIDSON);
+                SQD_TRY(launch_combine_inplace(ctx, w.Vb, N, m, w.Z, M, r, N));
+                SQD_TRY(launch_combine_inplace(ctx, w.Wb, N, m, w.Z, M, r, N));
+                // projected matrix and projections of t on the new basis
+                SQD_TRY(launch_project_g(ctx, w.G, M, m, w.Z, M, r, w.GZ));
+                SQD_TRY(launch_project_coeffs(ctx, w.Z, M, m, r, s1, s3));
+                SQD_CUDA(ctx, cudaMemcpyAsync(w.Vb + (int64_t)r * N, T, sizeof(double) * N,
+                                              cudaMemcpyDeviceToDevice, st));
+                prof_end(ctx, 4.0 * m * r * dN, 8.0 * (2.0 * m + 2.0 * r + 2.0) * dN);
+                P1 = s3;
+                m = r;
+                SQD_TRY(launch_identity_cols(ctx, w.Yprev, m, k, M));
+                mprev = m;
+                m_warm = 0;
+                T = w.Vb + (int64_t)m * N;
+            } else {
+                SQD_TRY(keep_coefficients());
+            }
+            grown = true;
+            // first update (with the second projections), then the second
+            prof_begin(ctx, PROF_ORTHO);
+            SQD_TRY(launch_gs_update_dot(ctx, MDf, w.Vb, N, m, P1, T, N, w.partial, nbr, s2));
+            prof_end(ctx, (4.0 * m + 3.0) * dN, 8.0 * (m + 2.0) * dN);
+            SQD_CUDA(ctx, cudaMemcpyAsync(hs, s2, sizeof(double) * (m + 1), cudaMemcpyDeviceToHost,
+                                          st));
+            SQD_CUDA(ctx, cudaStreamSynchronize(st));
+            const double n2a = hs[m];  // |t'|^2
+            double p2 = 0.0;
+            for (int i = 0; i < m; i++) p2 += hs[i] * hs[i];
+            const double n2b = n2a - p2;  // |t''|^2 by Pythagoras
+            int nacc = 1;
+            if (p2 <= 0.5 * n2a && n2b >= 1e-20) {
+                prof_begin(ctx, PROF_ORTHO);
+                SQD_TRY(launch_gs_update_scale(ctx, MDf, w.Vb, N, m, s2, 1.0 / std::sqrt(n2b), T, N,
+                                               nbr));
+                prof_end(ctx, (2.0 * m + 2.0) * dN, 8.0 * (m + 2.0) * dN);
+            } else {
+                // not safely resolved: second update, then the explicit norm
+                prof_begin(ctx, PROF_ORTHO);
+                SQD_TRY(launch_gemv_sub(ctx, w.Vb, N, m, s2, T, N));
+                prof_end(ctx, 2.0 * m * dN, 8.0 * (m + 2.0) * dN);
+                SQD_TRY(within_block(m, 1, &nacc));
+            }
+            if (nacc == 0) {
+                // the correction lies in the basis: the Ritz pair of the
+                // current basis is final (converged unless its residual is
+                // above the tolerance)
+                SQD_TRY(launch_jacobi_eigh(ctx, w.G, M, m, w.evals, w.evecs));
+                SQD_TRY(ritz_all());
+                x_ready = true;
+                if (!(rn[0] <= o->tol_residual)) status = SQD_EBREAKDOWN;
+                break;
+            }
+            m += 1;
+            SQD_TRY(apply_h(w.Vb + (int64_t)(m - 1) * N, w.Wb + (int64_t)(m - 1) * N, 1));
+            SQD_TRY(g_cols(m, m - 1, 1));
         }
-        const int m_old = m, b = (int)todo.size();
-        prof_begin(ctx, PROF_DAVIDSON);
-        for (int q = 0; q < b; q++) {
-            const int j = todo[q];
-            if (o->correction == 1)
-                SQD_TRY(launch_precondition_olsen(ctx, w.R + (int64_t)j * N, w.X + (int64_t)j * N,
-                                                  t->diag, theta[j], o->precond_floor, N,
-                                                  w.Vb + (int64_t)(m_old + q) * N, w.partial,
-                                                  w.tn2 + q));
-            else
-                SQD_TRY(launch_precondition_norm(ctx, w.R + (int64_t)j * N, t->diag, theta[j],
-                                                 o->precond_floor, N,
-                                                 w.Vb + (int64_t)(m_old + q) * N, w.partial,
-                                                 w.tn2 + q));
+        // the Ritz vector of the final eigensolve
+        if (!x_ready) {
+            prof_begin(ctx, PROF_DAVIDSON);
+            SQD_TRY(launch_combine(ctx, w.Vb, N, m, w.evecs, m, 1, w.X, N, N));
+            prof_end(ctx, 2.0 * m * dN, 8.0 * (m + 1.0) * dN);
         }
-        prof_end(ctx, 2.0 * b * dN, 24.0 * b * dN);
-        int nacc = 0;
-        SQD_TRY(orthonormalize_block(m_old, b, true, &nacc));
-        m = m_old + nacc;
-        if (nacc == 0) {
-            SQD_TRY(launch_jacobi_eigh(ctx, w.G, M, m, w.evals, w.evecs));
-            SQD_TRY(ritz_all());
-            bool res_ok = true;
-            for (int j = 0; j < k; j++) res_ok = res_ok && rn[j] <= o->tol_residual;
-            if (!res_ok) status = SQD_EBREAKDOWN;
-            break;
+    } else {
+        for (;;) {
+            prof_begin(ctx, PROF_EIGH);
+            SQD_TRY(launch_jacobi_eigh(ctx, w.G, M, m, w.evals, w.evecs, m_warm, w.Eold,
+                                       w.thold));
+            prof_end(ctx, 0.0, 0.0);
+            sel.clear();
+            for (int j = 0; j < k; j++)
+                if (!locked[j]) sel.push_back(j);
+            const bool full = sel.empty();
+            if (full)
+                for (int j = 0; j < k; j++) sel.push_back(j);
+            const int ks = (int)sel.size();
+            SQD_CUDA(ctx, cudaMemcpyAsync(w.sel, sel.data(), sizeof(int) * ks,
+                                          cudaMemcpyHostToDevice, st));
+            prof_begin(ctx, PROF_DAVIDSON);
+            SQD_TRY(launch_ritz_block(ctx, w.Vb, w.Wb, N, m, w.evecs, w.evals, w.sel, ks, w.X, w.R,
+                                      N, w.partial, nbr, w.dots));
+            prof_end(ctx, 4.0 * m * ks * dN + 2.0 * ks * dN, 8.0 * (2.0 * m + 2.0 * ks) * dN);
+            SQD_CUDA(ctx, cudaMemcpyAsync(theta.data(), w.evals, sizeof(double) * m,
+                                          cudaMemcpyDeviceToHost, st));
+            SQD_CUDA(ctx, cudaMemcpyAsync(rn2.data(), w.dots, sizeof(double) * ks,
+                                          cudaMemcpyDeviceToHost, st));
+            if (pend_f > 0.0)
+                SQD_CUDA(ctx, cudaMemcpyAsync(&gate_h, w.rdev + 1, sizeof(int),
+                                              cudaMemcpyDeviceToHost, st));
+            SQD_CUDA(ctx, cudaStreamSynchronize(st));
+            book_gated();
+            if (grown)
+                for (int j = 0; j < k; j++) dth[j] = std::fabs(theta[j] - theta_old[j]);
+            for (int j = 0; j < k; j++) theta_old[j] = theta[j];
+            bool all = true;
+            std::vector<int> todo;
+            for (int q = 0; q < ks; q++) {
+                const int j = sel[q];
+                rn[j] = std::sqrt(std::max(rn2[q], 0.0));
+                const bool c = rn[j] <= o->tol_residual && dth[j] <= o->tol_energy;
+                locked[j] = c ? 1 : 0;
+                if (!c) {
+                    all = false;
+                    todo.push_back(j);
+                }
+            }
+            if (full && all) break;
+            if (it >= o->max_iter) {
+                status = SQD_ENOTCONVERGED;
+                if (!full) SQD_TRY(ritz_all());
+                break;
+            }
+            it++;
+            grown = !todo.empty();
+            if (todo.empty()) continue;  // every root locked: check them all next
+            if (m + (int)todo.size() > M && (int64_t)m >= N) {
+                // the basis spans the whole space: the Ritz pairs are exact
+                SQD_TRY(ritz_all());
+                bool res_ok = true;
+                for (int j = 0; j < k; j++) res_ok = res_ok && rn[j] <= o->tol_residual;
+                if (!res_ok) status = SQD_EBREAKDOWN;
+                break;
+            }
+            if (m + (int)todo.size() > M) {
+                // restart (GD+k): the 2k lowest Ritz vectors plus the k Ritz
+                // vectors of the previous iteration, orthonormalised against them
+                int r = 0;
+                SQD_TRY(restart_basis(&r));
+                prof_begin(ctx, PROF_DAVIDSON);
+                SQD_TRY(launch_combine(ctx, w.Vb, N, m, w.Z, M, r, w.Tmp, N, N));
+                SQD_CUDA(ctx, cudaMemcpyAsync(w.Vb, w.Tmp, sizeof(double) * r * N,
+                                              cudaMemcpyDeviceToDevice, st));
+                SQD_TRY(launch_combine(ctx, w.Wb, N, m, w.Z, M, r, w.Tmp, N, N));
+                SQD_CUDA(ctx, cudaMemcpyAsync(w.Wb, w.Tmp, sizeof(double) * r * N,
+                                              cudaMemcpyDeviceToDevice, st));
+                // projected matrix of the new basis: G' = Z^T G Z
+                SQD_TRY(launch_project_g(ctx, w.G, M, m, w.Z, M, r, w.GZ));
+                prof_end(ctx, 4.0 * m * r * dN, 8.0 * (2.0 * m + 4.0 * r) * dN);
+                m = r;
+                // the current Ritz vectors are the first k basis vectors now
+                SQD_TRY(launch_identity_cols(ctx, w.Yprev, m, k, M));
+                mprev = m;
+                m_warm = 0;
+            } else {
+                SQD_TRY(keep_coefficients());
+            }
+            // room for the block (a restart of a space smaller than 4 nroots
+            // may leave less): the remaining roots are corrected next time
+            const int m_old = m, b = std::min((int)todo.size(), M - m);
+            if (b <= 0) return sqd_fail(ctx, SQD_EINVAL, "no room for a new block");
+            prof_begin(ctx, PROF_DAVIDSON);
+            for (int q = 0; q < b; q++) {
+                const int j = todo[q];
+                if (o->correction == 1)
+                    SQD_TRY(launch_precondition_olsen(ctx, w.R + (int64_t)j * N,
+                                                      w.X + (int64_t)j * N, t->diag, theta[j],
+                                                      o->precond_floor, N,
+                                                      w.Vb + (int64_t)(m_old + q) * N, w.partial,
+                                                      w.tn2 + q));
+                else
+                    SQD_TRY(launch_precondition_norm(ctx, w.R + (int64_t)j * N, t->diag, theta[j],
+                                                     o->precond_floor, N,
+                                                     w.Vb + (int64_t)(m_old + q) * N, w.partial,
+                                                     w.tn2 + q));
+            }
+            prof_end(ctx, 2.0 * b * dN, 24.0 * b * dN);
+            int nacc = 0;
+            SQD_TRY(orthonormalize_block(m_old, b, true, &nacc));
+            m = m_old + nacc;
+            if (nacc == 0) {
+                SQD_TRY(launch_jacobi_eigh(ctx, w.G, M, m, w.evals, w.evecs));
+                SQD_TRY(ritz_all());
+                bool res_ok = true;
+                for (int j = 0; j < k; j++) res_ok = res_ok && rn[j] <= o->tol_residual;
+                if (!res_ok) status = SQD_EBREAKDOWN;
+                break;
+            }
+            SQD_TRY(apply_h(w.Vb + (int64_t)m_old * N, w.Wb + (int64_t)m_old * N, nacc));
+            SQD_TRY(g_cols(m, m_old, nacc));
         }
-        SQD_TRY(apply_h(w.Vb + (int64_t)m_old * N, w.Wb + (int64_t)m_old * N, nacc));
-        SQD_TRY(g_cols(m, m_old, nacc));
     }
     // outputs: Ritz vectors with the phase fixed, energies, residuals
     SQD_CUDA(ctx, cudaMemcpyAsync(d_C, w.X, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, st));
@@ -902,8 +1141,11 @@ int sqd_davidson(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, double *h_en
     if (!ctx || !t || !o) return fail_noctx(SQD_EINVAL, "sqd_davidson: NULL argument");
     if (!h_energies || !d_C) return sqd_fail(ctx, SQD_EINVAL, "NULL output");
     const int64_t N = t->a.n * t->b->n;
-    if (o->nroots < 1 || o->nroots > 32 || o->nroots > N)
-        return sqd_fail(ctx, SQD_EINVAL, "nroots must be in [1, min(32, dimension)]");
+    if (o->nroots < 1 || o->nroots > SQD_MAX_ROOTS || o->nroots > N)
+        return sqd_fail(ctx, SQD_EINVAL,
+                        "nroots must be in [1, min(%d, dimension)] (the subspace is limited to "
+                        "%d vectors and a restart keeps 4 per root)",
+                        SQD_MAX_ROOTS, SQD_MAX_SUBSPACE);
     if (o->max_iter < 0 || !(o->tol_energy >= 0) || !(o->tol_residual >= 0) ||
         !(o->precond_floor > 0) || o->max_subspace < 0 || o->correction < 0 ||
         o->correction > 1)
@@ -974,6 +1216,35 @@ int sqd_davidson_batched(sqd_ctx *ctx, int nbatch, sqd_tables *const *tables,
         if (!tables[b]) return sqd_fail(ctx, SQD_EINVAL, "tables[%d] is NULL", b);
     SQD_TRY(use_device(ctx));
     return davidson_batched_impl(ctx, nbatch, tables, o, h_energies, d_C, h_iters, h_status);
+}
+
+int sqd_batched_set_tile(sqd_ctx *ctx, int entries_per_thread, double group_scale) {
+    if (!ctx) return fail_noctx(SQD_EINVAL, "sqd_batched_set_tile: NULL context");
+    if (entries_per_thread == 0) {
+        ctx->batched_force_ept = 0;
+        ctx->batched_force_scale = 0.0;
+        return SQD_OK;
+    }
+    if ((entries_per_thread != 8 && entries_per_thread != 16) ||
+        (group_scale != 0.5 && group_scale != 1.0 && group_scale != 2.0))
+        return sqd_fail(ctx, SQD_EINVAL,
+                        "tile must be 8 or 16 entries per thread with scale 0.5, 1 or 2");
+    ctx->batched_force_ept = entries_per_thread;
+    ctx->batched_force_scale = group_scale;
+    return SQD_OK;
+}
+
+int sqd_batched_tuning_buckets(const sqd_ctx *ctx, int max_buckets, int *nbuckets,
+                               int64_t *h_max_det, double *h_scale, int *h_entries) {
+    if (!ctx || !nbuckets) return fail_noctx(SQD_EINVAL, "sqd_batched_tuning_buckets: NULL argument");
+    const int nb = (int)ctx->batched_buckets.size();
+    *nbuckets = nb;
+    for (int q = 0; q < nb && q < max_buckets; q++) {
+        if (h_max_det) h_max_det[q] = ctx->batched_buckets[q].max_det;
+        if (h_scale) h_scale[q] = ctx->batched_buckets[q].scale;
+        if (h_entries) h_entries[q] = ctx->batched_buckets[q].entries_per_thread;
+    }
+    return SQD_OK;
 }
 
 int sqd_batched_tuning(const sqd_ctx *ctx, double *group_scale, int *device_loop) {

@@ -22,7 +22,51 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return r;  // valid in thread 0
 }
 
-#define JAC_MAX 112
+#define JAC_MAX SQD_MAX_SUBSPACE
+
+// Block sums of CNT per-thread values at once: shuffles within each warp,
+// one shared-memory exchange (sh holds (blockDim.x / 32) * CNT doubles), a
+// single barrier.  Thread i < CNT returns the block sum of value i through
+// *out_i and true; the others return false.  Summation order is fixed.
+template <int CNT>
+__device__ __forceinline__ bool block_sums(const double (&v)[CNT], double *sh, int *out_i,
+                                           double *out) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < CNT; i++) {
+        double x = v[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[w * CNT + i] = x;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x >= CNT) return false;
+    double s = 0.0;
+    for (int q = 0; q < nw; q++) s += sh[q * CNT + threadIdx.x];
+    *out_i = threadIdx.x;
+    *out = s;
+    return true;
+}
+
+// The preconditioner's 1 / (theta - H_II), |theta - H_II| clamped to floor_
+// (sign kept, + for 0).  GB300's FP64 pipe runs 4 flop per clock per SM, so
+// an IEEE division (a few tens of FP64 operations with its special cases)
+// costs more than the whole projection of a correction on a small basis.
+// Here: the hardware's approximate FP64 reciprocal (rcp.approx.ftz.f64, the
+// special-function unit) refined by two Newton-Raphson steps for 1/d,
+// x <- x + x (1 - d x), each of which squares the relative error; 4 DFMAs.
+// The correction vector needs no correctly rounded quotient: it is
+// orthonormalised against the basis afterwards, and the Davidson result
+// does not depend on its last bits.
+__device__ __forceinline__ double precond_recip(double d, double floor_) {
+    if (fabs(d) < floor_) d = (d < 0.0) ? -floor_ : floor_;
+    double x;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
+    double e = fma(-d, x, 1.0);
+    x = fma(x, e, x);
+    e = fma(-d, x, 1.0);
+    return fma(x, e, x);
+}
 
 // Warm start (m_old > 0): the first m_old basis vectors are unchanged since
 // the previous solve, whose eigenvectors E_old (m_old x m_old, column-major)

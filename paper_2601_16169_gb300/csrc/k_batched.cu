@@ -15,10 +15,19 @@
 //    reads, so the kernel sequence of an iteration is the same for every
 //    iteration and every subspace.  It is captured once in a CUDA graph and
 //    replayed; the host reads one counter (active subspaces) per replay.
-//  - The only tunable tile parameter (the number of alpha-row groups of the
-//    paired-singles kernel per subspace) is chosen at setup by timing the
-//    candidates on the subspaces' first sigma (autotuning).
-//  - One root per subspace (the ground state), GD+k restart to 3 vectors.
+//  - The paired-singles tile is autotuned at setup per size bucket (up to
+//    4 buckets of equal count by determinant count): the kernel variant (a
+//    persistent work-queue kernel with 16 entries per thread over 4096-entry
+//    chunks, or a plain grid with the single-problem tile, 8 entries per
+//    thread over 2048-entry chunks at 3 blocks per SM) and the alpha-row
+//    group count, timed on the first sigma of the bucket's largest subspaces.
+//  - One root per subspace (the ground state), at most 16 basis vectors,
+//    GD+k restart to 3 vectors.  The vector stages are the fused one-vector
+//    passes of the single-problem solver (4 m + 6 vector passes per
+//    iteration instead of 6 m + 14).
+//  - With profiling on, a one-warp kernel stamps the global timer at the
+//    stage boundaries inside the captured loop, so the sigma, vector and
+//    eigensolver stages are timed per iteration on the device.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -26,22 +35,24 @@
 #include "davidson_body.cuh"
 #include "sigma_body.cuh"
 
-#define BV_SLICE 8192  // vector elements per slice item
+#define BV_SLICE 32768  // vector elements per slice item (128 per thread)
 #define BV_THREADS 256
 
 struct bdesc {
     int64_t na, nb, N, nsl;
+    double sflops;  // algorithmic FP64 flops of one sigma (profiling)
     ss_args ssa;  // alpha side (C, S filled from the state)
     ss_args ssb;  // beta side on T -> U
-    ab_args ab;   // paired singles (C, S filled from the state)
-    int64_t nch, ngr;
-    double *V, *W, *X, *R, *T, *U;  // V, W: M vectors each
+    ab_args ab;   // paired singles over the wide chunks (persistent kernel)
+    ab_args abn;  // the same over the standard chunks (grid kernel)
+    int64_t nch, nchn, ngr;
+    double *V, *W, *X, *T, *U;  // V, W: M vectors each; T, U: sigma scratch
     double *G, *evals, *evecs, *Yprev, *Z, *partial, *coef;
     const double *diag;
 };
 
 struct bstate {
-    int m, mprev, active, status, it, restart, newvec, r;
+    int m, mprev, active, status, it, restart, newvec, r, expl;
     double theta, theta_old, rn, nrm2, scale;
     int64_t guess;
 };
@@ -151,6 +162,25 @@ __global__ void __launch_bounds__(AB_THREADS, KB_AB_MINB) kb_alpha_beta(const bd
     }
 }
 
+// the same stage as a plain grid over the items of the subspaces tuned to
+// it: the single-problem kernel's tile (standard chunks of AB_ECAP entries,
+// AB_EPT entries per thread, AB_MINB blocks per SM) with the subspace looked
+// up from the block index; blocks of subspaces without a new vector exit
+__global__ void __launch_bounds__(AB_THREADS, AB_MINB)
+    kb_alpha_beta_grid(const bdesc *__restrict__ D, const bstate *__restrict__ S,
+                       const int64_t *__restrict__ pre, int nprob) {
+    const int64_t item = blockIdx.x;
+    const int b = find_prob(pre, nprob, item);
+    if (!S[b].newvec) return;
+    const bdesc &d = D[b];
+    ab_args a = d.abn;
+    const int64_t slot = (int64_t)(S[b].m - 1) * d.N;
+    a.C = d.V + slot;
+    a.S = d.W + slot;
+    const int64_t local = item - pre[b];
+    alpha_beta_block_t<AB_EPT>(a, local % d.nchn, local / d.nchn);
+}
+
 // ---------------------------------------------------------- vector stages --
 
 // decode a slice item: problem, element range
@@ -168,61 +198,135 @@ __device__ __forceinline__ slice_t slice_of(const bdesc *D, const int64_t *pre, 
     return r;
 }
 
-// Ritz vector x = V y0, residual R = W y0 - theta x, partial |R|^2 per slice
-__global__ void __launch_bounds__(BV_THREADS) kb_ritz(const bdesc *__restrict__ D,
-                                                      const bstate *__restrict__ S,
-                                                      const int64_t *__restrict__ pre, int nprob) {
-    __shared__ double red[32];
+// The vector stages take the fused one-vector passes of the single-problem
+// solver (m <= BM basis vectors per subspace, BM = 16):
+//   kb_ritz_fused    : r = W y0 - theta V y0, t = r / (theta - H_II) into V[m]
+//                      (or T when the subspace restarts first), partials of
+//                      V_i . t, |r|^2, |t|^2 per slice;
+//   kb_state_check   : sums them; convergence, restart decision;
+//   kb_gs_update_dot : t' = t - V c with V_i . t' and |t'|^2;
+//   kb_gs_accept     : |t''|^2 = |t'|^2 - |V^T t'|^2 (Pythagoras) when that is
+//                      safely resolved, else the explicit norm is taken;
+//   kb_gs_update2    : t'' = (t' - V c') * s.
+// The Ritz vector itself is formed once, after the loop (kb_form_x).
+#define BM 16
+
+// The bodies are instantiated for the exact basis size MB of the block's
+// subspace (a block-uniform switch): a predicated-off FP64 instruction would
+// still take its FP64 issue slot, and the FP64 pipe bounds these passes.
+template <int N>
+struct bm_int {
+    static constexpr int value = N;
+};
+#define BM_CASE(N, f) \
+    case N:           \
+        f(bm_int<N>{}); \
+        break;
+#define BM_DISPATCH(m, f)                                                                    \
+    switch (m) {                                                                             \
+        BM_CASE(1, f) BM_CASE(2, f) BM_CASE(3, f) BM_CASE(4, f) BM_CASE(5, f) BM_CASE(6, f)  \
+        BM_CASE(7, f) BM_CASE(8, f) BM_CASE(9, f) BM_CASE(10, f) BM_CASE(11, f)             \
+        BM_CASE(12, f) BM_CASE(13, f) BM_CASE(14, f) BM_CASE(15, f)                         \
+        default: f(bm_int<16>{}); break;                                                     \
+    }
+
+// store the block sums of (projections [MB], extra [NX]) to rows 0..MB-1 and
+// MB..MB+NX-1 of the subspace's partials
+template <int MB, int NX>
+__device__ __forceinline__ void store_sums(const bdesc &d, int64_t slice, const double (&acc)[MB],
+                                           const double (&ex)[NX], double *red) {
+    double vals[MB + NX];
+#pragma unroll
+    for (int i = 0; i < MB; i++) vals[i] = acc[i];
+#pragma unroll
+    for (int i = 0; i < NX; i++) vals[MB + i] = ex[i];
+    int i;
+    double v;
+    if (block_sums<MB + NX>(vals, red, &i, &v)) d.partial[(int64_t)i * d.nsl + slice] = v;
+}
+
+template <int MB>
+__device__ __forceinline__ void ritz_fused_body(const bdesc &d, const slice_t &sl, int M,
+                                                double floor_, double *red) {
+    const double th = d.evals[0];
+    double *__restrict__ T = (MB + 1 > M) ? d.T : d.V + (int64_t)MB * d.N;
+    double acc[MB];
+#pragma unroll
+    for (int i = 0; i < MB; i++) acc[i] = 0.0;
+    double s_r = 0.0, s_t = 0.0;
+    for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) {
+        double vv[MB], ww[MB];
+#pragma unroll
+        for (int i = 0; i < MB; i++) {
+            vv[i] = d.V[(int64_t)i * d.N + n];
+            ww[i] = d.W[(int64_t)i * d.N + n];
+        }
+        double x0 = 0.0, x1 = 0.0, w0 = 0.0, w1 = 0.0;  // two chains each
+#pragma unroll
+        for (int i = 0; i < MB; i += 2) {
+            x0 = fma(vv[i], d.evecs[i], x0);
+            w0 = fma(ww[i], d.evecs[i], w0);
+            if (i + 1 < MB) {
+                x1 = fma(vv[i + 1], d.evecs[i + 1], x1);
+                w1 = fma(ww[i + 1], d.evecs[i + 1], w1);
+            }
+        }
+        const double r = fma(-th, x0 + x1, w0 + w1);
+        const double t = r * precond_recip(th - d.diag[n], floor_);
+        T[n] = t;
+        s_r = fma(r, r, s_r);
+        s_t = fma(t, t, s_t);
+#pragma unroll
+        for (int i = 0; i < MB; i++) acc[i] = fma(vv[i], t, acc[i]);
+    }
+    const double ex[2] = {s_r, s_t};
+    store_sums<MB, 2>(d, sl.s, acc, ex, red);
+}
+
+// partial layout per subspace: partial[i * nsl + slice]: rows 0..m-1 the
+// projections V_i . t, row m |r|^2, row m+1 |t|^2
+__global__ void __launch_bounds__(BV_THREADS) kb_ritz_fused(const bdesc *__restrict__ D,
+                                                            const bstate *__restrict__ S,
+                                                            const int64_t *__restrict__ pre,
+                                                            int nprob, int M, double floor_) {
+    __shared__ double red[(BV_THREADS / 32) * (BM + 2)];
     const slice_t sl = slice_of(D, pre, nprob, blockIdx.x);
     const bstate &st = S[sl.b];
     if (!st.active) return;
     const bdesc &d = D[sl.b];
-    const int m = st.m;
-    const double th = d.evals[0];
-    double ss = 0.0;
-    for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) {
-        double x = 0.0, w = 0.0;
-        int i = 0;
-        for (; i + 4 <= m; i += 4) {  // 8 loads in flight
-            double v[4], ww[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                v[u] = d.V[(int64_t)(i + u) * d.N + n];
-                ww[u] = d.W[(int64_t)(i + u) * d.N + n];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const double y = d.evecs[i + u];
-                x = fma(v[u], y, x);
-                w = fma(ww[u], y, w);
-            }
-        }
-        for (; i < m; i++) {
-            const double y = d.evecs[i];
-            x = fma(d.V[(int64_t)i * d.N + n], y, x);
-            w = fma(d.W[(int64_t)i * d.N + n], y, w);
-        }
-        const double r = fma(-th, x, w);
-        d.X[n] = x;
-        d.R[n] = r;
-        ss = fma(r, r, ss);
-    }
-    const double t = block_sum(ss, red);
-    if (threadIdx.x == 0) d.partial[sl.s] = t;
+    auto go = [&](auto mb) { ritz_fused_body<decltype(mb)::value>(d, sl, M, floor_, red); };
+    BM_DISPATCH(st.m, go);
 }
 
-// convergence test and restart decision (one thread per subspace)
-__global__ void kb_state_check(const bdesc *__restrict__ D, bstate *__restrict__ S, bparams P) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= P.nprob) return;
+// sum the slice partials of rows [0, cnt) into out (one block per subspace,
+// one thread per row, fixed order)
+__device__ __forceinline__ void sum_rows(const bdesc &d, int cnt, double *out) {
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        double s = 0.0;
+        for (int64_t k = 0; k < d.nsl; k++) s += d.partial[(int64_t)i * d.nsl + k];
+        out[i] = s;
+    }
+}
+
+// convergence test and restart decision (one block per subspace): the
+// projections V^T t go to coef, |r|^2 and |t|^2 to the state
+__global__ void __launch_bounds__(64) kb_state_check(const bdesc *__restrict__ D,
+                                                     bstate *__restrict__ S, bparams P) {
+    const int b = blockIdx.x;
     bstate &st = S[b];
-    st.newvec = 0;
-    st.restart = 0;
+    if (threadIdx.x == 0) {
+        st.newvec = 0;
+        st.restart = 0;
+    }
     if (!st.active) return;
     const bdesc &d = D[b];
-    double s = 0.0;
-    for (int64_t i = 0; i < d.nsl; i++) s += d.partial[i];
-    st.rn = sqrt(s);
+    const int m = st.m;
+    __shared__ double sums[BM + 2];
+    sum_rows(d, m + 2, sums);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) d.coef[i] = sums[i];
+    if (threadIdx.x != 0) return;
+    st.rn = sqrt(sums[m]);
     st.theta = d.evals[0];
     if (st.rn <= P.tol_r && fabs(st.theta - st.theta_old) <= P.tol_e) {
         st.active = 0;
@@ -274,11 +378,23 @@ __global__ void __launch_bounds__(128) kb_restart_basis(const bdesc *__restrict_
         for (int k = 0; k < m; k++) s = fma(d.Z[k + (int64_t)i * M], GZ[k + j * m], s);
         d.G[i + (int64_t)j * M] = s;
     }
+    // projections of the correction on the new basis V Z: Z^T coef
+    __shared__ double cz[3];
+    if (threadIdx.x < r) {
+        double s = 0.0;
+        for (int k = 0; k < m; k++) s = fma(d.Z[k + (int64_t)threadIdx.x * M], d.coef[k], s);
+        cz[threadIdx.x] = s;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         st.r = r;
         d.Yprev[0] = 1.0;
         for (int i = 1; i < r; i++) d.Yprev[i] = 0.0;
         st.mprev = r;
+        // the Ritz vector is the first new basis vector (for a later exit)
+        d.evecs[0] = 1.0;
+        for (int i = 1; i < r; i++) d.evecs[i] = 0.0;
+        for (int i = 0; i < r; i++) d.coef[i] = cz[i];
     }
 }
 
@@ -312,6 +428,7 @@ __global__ void __launch_bounds__(BV_THREADS) kb_restart_combine(const bdesc *__
                 d.W[(int64_t)j * d.N + n] = aw[j];
             }
         }
+        d.V[(int64_t)r * d.N + n] = d.T[n];  // the correction, formed before the restart
     }
 }
 
@@ -322,26 +439,111 @@ __global__ void kb_restart_finish(bstate *__restrict__ S, int nprob) {
     if (st.active && st.restart) st.m = st.r;
 }
 
-// correction t = R / (theta - H_II) into V[m]
-__global__ void __launch_bounds__(BV_THREADS) kb_precondition(const bdesc *__restrict__ D,
-                                                              const bstate *__restrict__ S,
-                                                              const int64_t *__restrict__ pre,
-                                                              int nprob, double floor_) {
+template <int MB>
+__device__ __forceinline__ void gs_update_dot_body(const bdesc &d, const slice_t &sl,
+                                                   double *red) {
+    double *__restrict__ T = d.V + (int64_t)MB * d.N;
+    double acc[MB];
+#pragma unroll
+    for (int i = 0; i < MB; i++) acc[i] = 0.0;
+    double s_t = 0.0;
+    for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) {
+        double vv[MB];
+#pragma unroll
+        for (int i = 0; i < MB; i++) vv[i] = d.V[(int64_t)i * d.N + n];
+        const double t0 = T[n];
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int i = 0; i < MB; i += 2) {
+            s0 = fma(vv[i], d.coef[i], s0);
+            if (i + 1 < MB) s1 = fma(vv[i + 1], d.coef[i + 1], s1);
+        }
+        const double t = t0 - (s0 + s1);
+        T[n] = t;
+        s_t = fma(t, t, s_t);
+#pragma unroll
+        for (int i = 0; i < MB; i++) acc[i] = fma(vv[i], t, acc[i]);
+    }
+    const double ex[1] = {s_t};
+    store_sums<MB, 1>(d, sl.s, acc, ex, red);
+}
+
+// t' = t - V coef (t = V[m]) with partials of V_i . t' (rows 0..m-1) and
+// |t'|^2 (row m)
+__global__ void __launch_bounds__(BV_THREADS) kb_gs_update_dot(const bdesc *__restrict__ D,
+                                                               const bstate *__restrict__ S,
+                                                               const int64_t *__restrict__ pre,
+                                                               int nprob) {
+    __shared__ double red[(BV_THREADS / 32) * (BM + 1)];
     const slice_t sl = slice_of(D, pre, nprob, blockIdx.x);
     const bstate &st = S[sl.b];
     if (!st.active) return;
     const bdesc &d = D[sl.b];
-    double *t = d.V + (int64_t)st.m * d.N;
-    for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) {
-        double den = st.theta - d.diag[n];
-        if (fabs(den) < floor_) den = (den < 0.0) ? -floor_ : floor_;
-        t[n] = d.R[n] / den;
+    auto go = [&](auto mb) { gs_update_dot_body<decltype(mb)::value>(d, sl, red); };
+    BM_DISPATCH(st.m, go);
+}
+
+// second-pass coefficients; the norm after the second pass by Pythagoras
+// where safely resolved (else expl = 1: the norm is taken explicitly)
+__global__ void __launch_bounds__(64) kb_gs_accept(const bdesc *__restrict__ D,
+                                                   bstate *__restrict__ S) {
+    const int b = blockIdx.x;
+    bstate &st = S[b];
+    if (!st.active) return;
+    const bdesc &d = D[b];
+    const int m = st.m;
+    __shared__ double sums[BM + 1];
+    sum_rows(d, m + 1, sums);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) d.coef[i] = sums[i];
+    if (threadIdx.x != 0) return;
+    double p2 = 0.0;
+    for (int i = 0; i < m; i++) p2 += sums[i] * sums[i];
+    const double n2a = sums[m], n2b = n2a - p2;
+    if (p2 <= 0.5 * n2a && n2b >= 1e-20) {
+        st.expl = 0;
+        st.scale = 1.0 / sqrt(n2b);
+    } else {
+        st.expl = 1;
+        st.scale = 1.0;
     }
 }
 
-// partial dot products on a slice.  mode 0: V[i] . V[m], i < m (Gram-Schmidt
-// coefficients); mode 1: V[m] . V[m] (norm); mode 2: V[i] . W[m-1], i < m
-// (new column of G, after m was incremented)
+template <int MB>
+__device__ __forceinline__ void gs_update2_body(const bdesc &d, const slice_t &sl, double sc) {
+    double *__restrict__ T = d.V + (int64_t)MB * d.N;
+    for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) {
+        double vv[MB];
+#pragma unroll
+        for (int i = 0; i < MB; i++) vv[i] = d.V[(int64_t)i * d.N + n];
+        const double t0 = T[n];
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int i = 0; i < MB; i += 2) {
+            s0 = fma(vv[i], d.coef[i], s0);
+            if (i + 1 < MB) s1 = fma(vv[i + 1], d.coef[i + 1], s1);
+        }
+        T[n] = (t0 - (s0 + s1)) * sc;
+    }
+}
+
+// t'' = (t' - V coef) * scale
+__global__ void __launch_bounds__(BV_THREADS) kb_gs_update2(const bdesc *__restrict__ D,
+                                                            const bstate *__restrict__ S,
+                                                            const int64_t *__restrict__ pre,
+                                                            int nprob) {
+    const slice_t sl = slice_of(D, pre, nprob, blockIdx.x);
+    const bstate &st = S[sl.b];
+    if (!st.active) return;
+    const bdesc &d = D[sl.b];
+    const double sc = st.scale;
+    auto go = [&](auto mb) { gs_update2_body<decltype(mb)::value>(d, sl, sc); };
+    BM_DISPATCH(st.m, go);
+}
+
+// partial dot products on a slice.  mode 1: V[m] . V[m] (the explicit norm,
+// subspaces with expl set); mode 2: V[i] . W[m-1], i < m (new column of G,
+// after m was incremented)
 __global__ void __launch_bounds__(BV_THREADS) kb_gram(const bdesc *__restrict__ D,
                                                       const bstate *__restrict__ S,
                                                       const int64_t *__restrict__ pre, int nprob,
@@ -349,7 +551,7 @@ __global__ void __launch_bounds__(BV_THREADS) kb_gram(const bdesc *__restrict__ 
     __shared__ double red[32];
     const slice_t sl = slice_of(D, pre, nprob, blockIdx.x);
     const bstate &st = S[sl.b];
-    if (mode == 2 ? !st.newvec : !st.active) return;
+    if (mode == 2 ? !st.newvec : !(st.active && st.expl)) return;
     const bdesc &d = D[sl.b];
     const int m = st.m;
     const double *x = (mode == 2) ? d.W + (int64_t)(m - 1) * d.N : d.V + (int64_t)m * d.N;
@@ -383,41 +585,14 @@ __global__ void kb_gram_final(const bdesc *__restrict__ D, bstate *__restrict__ 
                               int M) {
     const int b = blockIdx.x;
     bstate &st = S[b];
-    if (mode == 2 ? !st.newvec : !st.active) return;
+    if (mode == 2 ? !st.newvec : !(st.active && st.expl)) return;
     const bdesc &d = D[b];
     const int cnt = (mode == 1) ? 1 : st.m;
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
         double s = 0.0;
         for (int64_t k = 0; k < d.nsl; k++) s += d.partial[(int64_t)i * d.nsl + k];
-        if (mode == 0) d.coef[i] = s;
-        else if (mode == 1) st.nrm2 = s;
+        if (mode == 1) st.nrm2 = s;
         else d.G[i + (int64_t)(st.m - 1) * M] = s;
-    }
-}
-
-// V[m] -= sum_i coef_i V[i]
-__global__ void __launch_bounds__(BV_THREADS) kb_project_out(const bdesc *__restrict__ D,
-                                                             const bstate *__restrict__ S,
-                                                             const int64_t *__restrict__ pre,
-                                                             int nprob) {
-    const slice_t sl = slice_of(D, pre, nprob, blockIdx.x);
-    const bstate &st = S[sl.b];
-    if (!st.active) return;
-    const bdesc &d = D[sl.b];
-    const int m = st.m;
-    double *t = d.V + (int64_t)m * d.N;
-    for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) {
-        double s = 0.0;
-        int i = 0;
-        for (; i + 8 <= m; i += 8) {  // 8 loads in flight
-            double a[8];
-#pragma unroll
-            for (int u = 0; u < 8; u++) a[u] = d.V[(int64_t)(i + u) * d.N + n];
-#pragma unroll
-            for (int u = 0; u < 8; u++) s = fma(a[u], d.coef[i + u], s);
-        }
-        for (; i < m; i++) s = fma(d.V[(int64_t)i * d.N + n], d.coef[i], s);
-        t[n] -= s;
     }
 }
 
@@ -428,6 +603,11 @@ __global__ void kb_state_accept(bstate *__restrict__ S, bparams P) {
     bstate &st = S[b];
     st.newvec = 0;
     if (!st.active) return;
+    if (!st.expl) {  // normalised in kb_gs_update2
+        st.m++;
+        st.newvec = 1;
+        return;
+    }
     const double nrm = sqrt(st.nrm2);
     if (nrm >= 1e-12) {
         st.scale = 1.0 / nrm;
@@ -439,16 +619,33 @@ __global__ void kb_state_accept(bstate *__restrict__ S, bparams P) {
     }
 }
 
+// normalise a correction whose norm was taken explicitly
 __global__ void __launch_bounds__(BV_THREADS) kb_scale_new(const bdesc *__restrict__ D,
                                                            const bstate *__restrict__ S,
                                                            const int64_t *__restrict__ pre,
                                                            int nprob) {
     const slice_t sl = slice_of(D, pre, nprob, blockIdx.x);
     const bstate &st = S[sl.b];
-    if (!st.newvec) return;
+    if (!st.newvec || !st.expl) return;
     const bdesc &d = D[sl.b];
     double *v = d.V + (int64_t)(st.m - 1) * d.N;
     for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) v[n] *= st.scale;
+}
+
+// the Ritz vector of the final eigensolve, X = V y0 (after the loop)
+__global__ void __launch_bounds__(BV_THREADS) kb_form_x(const bdesc *__restrict__ D,
+                                                        const bstate *__restrict__ S,
+                                                        const int64_t *__restrict__ pre,
+                                                        int nprob) {
+    const slice_t sl = slice_of(D, pre, nprob, blockIdx.x);
+    const bstate &st = S[sl.b];
+    const bdesc &d = D[sl.b];
+    const int m = st.m;
+    for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) {
+        double x = 0.0;
+        for (int i = 0; i < m; i++) x = fma(d.V[(int64_t)i * d.N + n], d.evecs[i], x);
+        d.X[n] = x;
+    }
 }
 
 __global__ void __launch_bounds__(256) kb_jacobi(const bdesc *__restrict__ D,
@@ -465,6 +662,54 @@ __global__ void kb_loop_control(const int *__restrict__ active, int *__restrict_
                                 int limit, cudaGraphConditionalHandle h) {
     const int it = ++(*iters);
     cudaGraphSetConditional(h, (*active > 0 && it < limit) ? 1u : 0u);
+}
+
+// Stage timer of the batched loop (profiling only; one warp).  Stamped at
+// the stage boundaries inside the captured loop: the global-timer interval
+// since the previous stamp is booked to `stage` (0 sigma, 1 vector work,
+// 2 eigensolve; -1 only sets the start), with the algorithmic work of the
+// subspaces the stage served: sigma flops of those given a new vector;
+// vector bytes and flops of the one-vector Davidson step (Ritz pair, residual,
+// correction, two Gram-Schmidt passes, normalisation in three fused passes:
+// 4 m + 6 vector passes and 12 m + 12 flops per element; part 1) or of the
+// new G column (m + 1 passes, 2 m flops; part 2).
+// acc: [0..3) ns, [3..6) flops, [6..9) bytes, [9..12) regions, [12] last stamp
+__global__ void kb_stamp(const bdesc *__restrict__ D, const bstate *__restrict__ S, int nprob,
+                         int stage, int part, double *__restrict__ acc) {
+    unsigned long long now;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+    double f = 0.0, by = 0.0;
+    if (stage >= 0) {
+        for (int b = threadIdx.x; b < nprob; b += 32) {
+            if (!S[b].newvec) continue;
+            const double N = (double)D[b].N;
+            const int m = S[b].m;  // after the new vector was appended
+            if (stage == 0) {
+                f += D[b].sflops;
+            } else if (stage == 1 && part == 1) {
+                by += 8.0 * N * (4.0 * (m - 1) + 6.0);
+                f += N * (12.0 * (m - 1) + 12.0);
+            } else if (stage == 1) {
+                by += 8.0 * N * (m + 1.0);
+                f += 2.0 * N * m;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            f += __shfl_down_sync(0xffffffffu, f, o);
+            by += __shfl_down_sync(0xffffffffu, by, o);
+        }
+    }
+    if (threadIdx.x == 0) {
+        unsigned long long *last = reinterpret_cast<unsigned long long *>(acc + 12);
+        if (stage >= 0) {
+            acc[stage] += (double)(now - *last);
+            acc[3 + stage] += f;
+            acc[6 + stage] += by;
+            if (stage != 1 || part == 1) acc[9 + stage] += 1.0;
+        }
+        *last = now;
+    }
 }
 
 __global__ void kb_count_active(const bstate *__restrict__ S, int nprob, int *out) {
@@ -524,12 +769,15 @@ __global__ void __launch_bounds__(256) kb_guess(const bdesc *__restrict__ D,
 
 struct batched_plan {
     int nprob = 0, M = 0;
+    double *stamps = nullptr;  // stage timer accumulators (profiling), 13 doubles
     std::vector<bdesc> hdesc;
     bdesc *D = nullptr;
     bstate *S = nullptr;
     int64_t *pre_ssa = nullptr, *pre_ssb = nullptr, *pre_ab = nullptr, *pre_t0 = nullptr,
             *pre_t1 = nullptr, *pre_vec = nullptr;
     int64_t tot_vec = 0;
+    int64_t *pre_abg = nullptr;    // item prefix of the grid paired-singles kernel
+    int64_t ab_items[2] = {0, 0};  // items of the persistent (0) and grid (1) kernels
     unsigned long long *counters = nullptr;  // 5 persistent-kernel queues
     int *d_active = nullptr;
     std::vector<void *> owned;  // device allocations
@@ -581,6 +829,23 @@ __global__ void kb_zero_counters(unsigned long long *c, int n) {
     if ((int)threadIdx.x < n) c[threadIdx.x] = 0ull;
 }
 
+// the paired-singles stage: the persistent kernel for the subspaces tuned
+// to the wide tile, the grid kernel for the others
+static int launch_ab_stage(sqd_ctx *ctx, batched_plan &p) {
+    const size_t shm = sizeof(double) * 2 * AB_NA * AB_YW;
+    if (p.ab_items[0] > 0) {
+        kb_alpha_beta<<<KB_AB_MINB * ctx->sm_count, AB_THREADS, shm, ctx->stream>>>(
+            p.D, p.S, p.pre_ab, p.nprob, p.counters + 2);
+        SQD_LAUNCHED(ctx);
+    }
+    if (p.ab_items[1] > 0) {
+        kb_alpha_beta_grid<<<(unsigned)p.ab_items[1], AB_THREADS, shm, ctx->stream>>>(
+            p.D, p.S, p.pre_abg, p.nprob);
+        SQD_LAUNCHED(ctx);
+    }
+    return SQD_OK;
+}
+
 // launch the three sigma stages for every subspace flagged newvec (kernels
 // only, so the sequence can be the body of a conditional graph node)
 static int launch_sigma_stages(sqd_ctx *ctx, batched_plan &p) {
@@ -593,10 +858,7 @@ static int launch_sigma_stages(sqd_ctx *ctx, batched_plan &p) {
     kb_transpose<0><<<8 * sm, dim3(32, 8), 0, ctx->stream>>>(p.D, p.S, p.pre_t0, n,
                                                              p.counters + 1);
     SQD_LAUNCHED(ctx);
-    const size_t shm = sizeof(double) * 2 * AB_NA * AB_YW;
-    kb_alpha_beta<<<KB_AB_MINB * sm, AB_THREADS, shm, ctx->stream>>>(p.D, p.S, p.pre_ab, n,
-                                                             p.counters + 2);
-    SQD_LAUNCHED(ctx);
+    SQD_TRY(launch_ab_stage(ctx, p));
     kb_same_spin<false><<<8 * sm, 256, 0, ctx->stream>>>(p.D, p.S, p.pre_ssb, n,
                                                          p.counters + 3);
     SQD_LAUNCHED(ctx);
@@ -615,17 +877,26 @@ static int launch_gram(sqd_ctx *ctx, batched_plan &p, int mode) {
     return SQD_OK;
 }
 
+static int stamp(sqd_ctx *ctx, batched_plan &p, int stage, int part = 0) {
+    if (!p.stamps) return SQD_OK;
+    kb_stamp<<<1, 32, 0, ctx->stream>>>(p.D, p.S, p.nprob, stage, part, p.stamps);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
 // one Davidson iteration for every active subspace (the captured sequence)
 static int launch_iteration(sqd_ctx *ctx, batched_plan &p, const bparams &P) {
     const int n = p.nprob;
     const unsigned vb = (unsigned)p.tot_vec;
     const unsigned tb = (unsigned)((n + 127) / 128);
     const size_t jshm = sizeof(double) * 2 * (size_t)((p.M + 1) & ~1) * (((p.M + 1) & ~1) + 1);
+    SQD_TRY(stamp(ctx, p, -1));
     kb_jacobi<<<n, 256, jshm, ctx->stream>>>(p.D, p.S, p.M);
     SQD_LAUNCHED(ctx);
-    kb_ritz<<<vb, BV_THREADS, 0, ctx->stream>>>(p.D, p.S, p.pre_vec, n);
+    SQD_TRY(stamp(ctx, p, 2));
+    kb_ritz_fused<<<vb, BV_THREADS, 0, ctx->stream>>>(p.D, p.S, p.pre_vec, n, p.M, P.floor_);
     SQD_LAUNCHED(ctx);
-    kb_state_check<<<tb, 128, 0, ctx->stream>>>(p.D, p.S, P);
+    kb_state_check<<<n, 64, 0, ctx->stream>>>(p.D, p.S, P);
     SQD_LAUNCHED(ctx);
     kb_restart_basis<<<n, 128, 0, ctx->stream>>>(p.D, p.S, P);
     SQD_LAUNCHED(ctx);
@@ -633,47 +904,91 @@ static int launch_iteration(sqd_ctx *ctx, batched_plan &p, const bparams &P) {
     SQD_LAUNCHED(ctx);
     kb_restart_finish<<<tb, 128, 0, ctx->stream>>>(p.S, n);
     SQD_LAUNCHED(ctx);
-    kb_precondition<<<vb, BV_THREADS, 0, ctx->stream>>>(p.D, p.S, p.pre_vec, n, P.floor_);
+    kb_gs_update_dot<<<vb, BV_THREADS, 0, ctx->stream>>>(p.D, p.S, p.pre_vec, n);
     SQD_LAUNCHED(ctx);
-    for (int pass = 0; pass < 2; pass++) {
-        SQD_TRY(launch_gram(ctx, p, 0));
-        kb_project_out<<<vb, BV_THREADS, 0, ctx->stream>>>(p.D, p.S, p.pre_vec, n);
-        SQD_LAUNCHED(ctx);
-    }
-    SQD_TRY(launch_gram(ctx, p, 1));
+    kb_gs_accept<<<n, 64, 0, ctx->stream>>>(p.D, p.S);
+    SQD_LAUNCHED(ctx);
+    kb_gs_update2<<<vb, BV_THREADS, 0, ctx->stream>>>(p.D, p.S, p.pre_vec, n);
+    SQD_LAUNCHED(ctx);
+    SQD_TRY(launch_gram(ctx, p, 1));  // explicit norms only where Pythagoras was not safe
     kb_state_accept<<<tb, 128, 0, ctx->stream>>>(p.S, P);
     SQD_LAUNCHED(ctx);
     kb_scale_new<<<vb, BV_THREADS, 0, ctx->stream>>>(p.D, p.S, p.pre_vec, n);
     SQD_LAUNCHED(ctx);
+    SQD_TRY(stamp(ctx, p, 1, 1));
     SQD_TRY(launch_sigma_stages(ctx, p));
+    SQD_TRY(stamp(ctx, p, 0));
     SQD_TRY(launch_gram(ctx, p, 2));
     kb_count_active<<<1, 256, 0, ctx->stream>>>(p.S, n, p.d_active);
     SQD_LAUNCHED(ctx);
+    SQD_TRY(stamp(ctx, p, 1, 2));
     return SQD_OK;
 }
 
-// paired-singles item prefix for a given group scale; updates descriptors
-static int set_groups(sqd_ctx *ctx, batched_plan &p, const std::vector<sqd_tables *> &tabs,
-                      double scale) {
-    std::vector<int64_t> pre{0};
+// Tile choices of the paired-singles stage, per subspace: the kernel
+// variant (0: persistent, wide chunks of AB_ECAP_WIDE entries, 16 per
+// thread, 2 blocks per SM; 1: grid, standard chunks, AB_EPT per thread,
+// AB_MINB blocks per SM) and the alpha-row group count (the table's default
+// split times a scale).  Group arrays are built once per candidate scale.
+static const double kAbScales[] = {0.5, 1.0, 2.0};
+#define AB_NSCALE 3
+
+struct ab_choice {
+    std::vector<int64_t *> groups;  // per scale: device group rows
+    std::vector<int64_t> ngr;       // per scale: group count
+};
+
+static int build_choices(sqd_ctx *ctx, batched_plan &p, const std::vector<sqd_tables *> &tabs,
+                         std::vector<ab_choice> &ch) {
+    ch.resize(p.nprob);
     for (int b = 0; b < p.nprob; b++) {
         const sqd_tables *t = tabs[b];
         // relative to the default split (the table's own split may be tuned)
         const double base = t->ab.ngroups / (t->ab.scale > 0.0 ? t->ab.scale : 1.0);
-        int64_t ng = (int64_t)std::llround(std::max(1.0, base * scale));
-        if (ng > t->a.n) ng = std::max<int64_t>(1, t->a.n);
-        std::vector<int64_t> g = alpha_groups(&t->a, ng);
-        int64_t *dg = nullptr;
-        SQD_TRY(plan_alloc(ctx, p, (void **)&dg, sizeof(int64_t) * g.size()));
-        SQD_CUDA(ctx, cudaMemcpy(dg, g.data(), sizeof(int64_t) * g.size(), cudaMemcpyHostToDevice));
-        bdesc &d = p.hdesc[b];
-        d.ab.group_rows = dg;
-        d.ngr = (int64_t)g.size() - 1;
-        const int64_t items = (t->a.nnz1 > 0 && t->b->nnz1 > 0) ? d.nch * d.ngr : 0;
-        pre.push_back(pre.back() + items);
+        for (int k = 0; k < AB_NSCALE; k++) {
+            int64_t ng = (int64_t)std::llround(std::max(1.0, base * kAbScales[k]));
+            if (ng > t->a.n) ng = std::max<int64_t>(1, t->a.n);
+            std::vector<int64_t> g = alpha_groups(&t->a, ng);
+            int64_t *dg = nullptr;
+            SQD_TRY(plan_alloc(ctx, p, (void **)&dg, sizeof(int64_t) * g.size()));
+            SQD_CUDA(ctx, cudaMemcpyAsync(dg, g.data(), sizeof(int64_t) * g.size(),
+                                          cudaMemcpyHostToDevice, ctx->stream));
+            SQD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            ch[b].groups.push_back(dg);
+            ch[b].ngr.push_back((int64_t)g.size() - 1);
+        }
     }
-    SQD_CUDA(ctx, cudaMemcpy(p.D, p.hdesc.data(), sizeof(bdesc) * p.nprob, cudaMemcpyHostToDevice));
-    SQD_TRY(upload_prefix(ctx, p, pre, &p.pre_ab));
+    SQD_TRY(plan_alloc(ctx, p, (void **)&p.pre_ab, sizeof(int64_t) * (p.nprob + 1)));
+    SQD_TRY(plan_alloc(ctx, p, (void **)&p.pre_abg, sizeof(int64_t) * (p.nprob + 1)));
+    return SQD_OK;
+}
+
+// apply (variant, scale index) per subspace; `on` (optional) limits the
+// paired-singles items to the flagged subspaces (tuning)
+static int apply_choices(sqd_ctx *ctx, batched_plan &p, const std::vector<sqd_tables *> &tabs,
+                         const std::vector<ab_choice> &ch, const std::vector<int> &var,
+                         const std::vector<int> &sck, const std::vector<char> *on) {
+    std::vector<int64_t> pre0{0}, pre1{0};
+    for (int b = 0; b < p.nprob; b++) {
+        const sqd_tables *t = tabs[b];
+        bdesc &d = p.hdesc[b];
+        d.ab.group_rows = d.abn.group_rows = ch[b].groups[sck[b]];
+        d.ngr = ch[b].ngr[sck[b]];
+        const bool has = t->a.nnz1 > 0 && t->b->nnz1 > 0 && (!on || (*on)[b]);
+        pre0.push_back(pre0.back() + ((has && var[b] == 0) ? d.nch * d.ngr : 0));
+        pre1.push_back(pre1.back() + ((has && var[b] == 1) ? d.nchn * d.ngr : 0));
+    }
+    p.ab_items[0] = pre0.back();
+    p.ab_items[1] = pre1.back();
+    if (p.ab_items[1] > 2147483647LL) return sqd_fail(ctx, SQD_EINVAL, "batch too large");
+    cudaStream_t st = ctx->stream;
+    SQD_CUDA(ctx, cudaMemcpyAsync(p.D, p.hdesc.data(), sizeof(bdesc) * p.nprob,
+                                  cudaMemcpyHostToDevice, st));
+    SQD_CUDA(ctx, cudaMemcpyAsync(p.pre_ab, pre0.data(), sizeof(int64_t) * pre0.size(),
+                                  cudaMemcpyHostToDevice, st));
+    SQD_CUDA(ctx, cudaMemcpyAsync(p.pre_abg, pre1.data(), sizeof(int64_t) * pre1.size(),
+                                  cudaMemcpyHostToDevice, st));
+    SQD_CUDA(ctx, cudaStreamSynchronize(st));
     return SQD_OK;
 }
 
@@ -682,7 +997,10 @@ int davidson_batched_impl(sqd_ctx *ctx, int nprob, sqd_tables *const *tables,
                           int *h_iters, int *h_status) {
     batched_plan p;
     p.nprob = nprob;
-    p.M = o->max_subspace > 0 ? std::min(o->max_subspace, 112) : 16;
+    // at most BM = 16 basis vectors per subspace (the fused vector passes
+    // keep the projections in registers; a larger one-root basis did not
+    // reduce the iterations: 176 / 175 / 174 at 16 / 24 / 32 on 4e8 dets)
+    p.M = o->max_subspace > 0 ? std::min(o->max_subspace, BM) : BM;
     if (p.M < 4) return sqd_fail(ctx, SQD_EINVAL, "max_subspace must be >= 4");
     std::vector<sqd_tables *> tabs(tables, tables + nprob);
     p.hdesc.resize(nprob);
@@ -711,7 +1029,6 @@ int davidson_batched_impl(sqd_ctx *ctx, int nprob, sqd_tables *const *tables,
         BA(V, (int64_t)M * d.N);
         BA(W, (int64_t)M * d.N);
         BA(X, d.N);
-        BA(R, d.N);
         BA(T, d.N);
         BA(U, d.N);
         BA(G, (int64_t)M * M);
@@ -719,7 +1036,7 @@ int davidson_batched_impl(sqd_ctx *ctx, int nprob, sqd_tables *const *tables,
         BA(evecs, (int64_t)M * M);
         BA(Yprev, M);
         BA(Z, (int64_t)M * 3);
-        BA(partial, (int64_t)M * d.nsl);
+        BA(partial, (int64_t)(M + 2) * d.nsl);
         BA(coef, M);
 #undef BA
         if ((rc = (cudaMemsetAsync(d.V, 0, sizeof(double) * d.N, ctx->stream) == cudaSuccess
@@ -731,10 +1048,17 @@ int davidson_batched_impl(sqd_ctx *ctx, int nprob, sqd_tables *const *tables,
         d.ssa = make_ss_args(&t->a, t->b, d.na, d.nb, nullptr, nullptr, t->diag);
         d.ssb = make_ss_args(t->b, &t->a, d.nb, d.na, nullptr, nullptr, nullptr);
         d.ab = make_ab_args(t, nullptr, nullptr);
-        // the persistent kernel runs 2 blocks per SM with 16 entries per thread
+        {
+            double fa, fb, fab;
+            sigma_work(t, &fa, &fb, &fab);
+            d.sflops = fa + fb + fab;
+        }
+        // persistent kernel: wide chunks; grid kernel: the standard ones
+        d.abn = d.ab;
         d.ab.chunk_e = t->ab.chunk_e_wide;
         d.ab.chunk_y = t->ab.chunk_y_wide;
         d.nch = t->ab.nchunks_wide;
+        d.nchn = t->ab.nchunks;
         d.ngr = t->ab.ngroups;
         pssa.push_back(pssa.back() + d.na * ((d.nb + 255) / 256));
         pssb.push_back(pssb.back() + d.nb * ((d.na + 255) / 256));
@@ -749,6 +1073,12 @@ int davidson_batched_impl(sqd_ctx *ctx, int nprob, sqd_tables *const *tables,
     if ((rc = plan_alloc(ctx, p, (void **)&p.counters, sizeof(unsigned long long) * 8)) != SQD_OK)
         return fail(rc);
     if ((rc = plan_alloc(ctx, p, (void **)&p.d_active, sizeof(int))) != SQD_OK) return fail(rc);
+    if (ctx->prof) {
+        if ((rc = plan_alloc(ctx, p, (void **)&p.stamps, sizeof(double) * 13)) != SQD_OK)
+            return fail(rc);
+        if (cudaMemsetAsync(p.stamps, 0, sizeof(double) * 13, ctx->stream) != cudaSuccess)
+            return fail(sqd_fail(ctx, SQD_ECUDA, "memset failed"));
+    }
     if ((rc = upload_prefix(ctx, p, pssa, &p.pre_ssa)) != SQD_OK) return fail(rc);
     if ((rc = upload_prefix(ctx, p, pssb, &p.pre_ssb)) != SQD_OK) return fail(rc);
     if ((rc = upload_prefix(ctx, p, pt0, &p.pre_t0)) != SQD_OK) return fail(rc);
@@ -761,40 +1091,103 @@ int davidson_batched_impl(sqd_ctx *ctx, int nprob, sqd_tables *const *tables,
     const size_t jshm = sizeof(double) * 2 * (size_t)MM * (MM + 1);
     if (cudaFuncSetAttribute(kb_alpha_beta, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)abshm) != cudaSuccess ||
+        cudaFuncSetAttribute(kb_alpha_beta_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)abshm) != cudaSuccess ||
         cudaFuncSetAttribute(kb_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)jshm) != cudaSuccess)
         return fail(sqd_fail(ctx, SQD_ECUDA, "cannot set shared memory limits"));
 
-    // --- autotune the paired-singles group scale on the first sigma -----
-    const double cand[] = {0.125, 0.25, 0.5, 1.0};
-    double best_ms = INFINITY, best = 1.0;
+    // --- autotune the paired-singles tile per size bucket ------------------
+    // The subspaces are split into up to 4 buckets of equal count by
+    // determinant count.  For each bucket, every (kernel variant, group
+    // scale) pair is timed on the paired-singles stage of the first sigma of
+    // up to 4 of its largest subspaces; the fastest is kept for the bucket.
+    std::vector<ab_choice> ch;
+    if ((rc = build_choices(ctx, p, tabs, ch)) != SQD_OK) return fail(rc);
+    std::vector<int> order(nprob);
+    for (int b = 0; b < nprob; b++) order[b] = b;
+    std::sort(order.begin(), order.end(),
+              [&](int x, int y) { return p.hdesc[x].N < p.hdesc[y].N; });
+    const int nbk = std::min(4, nprob);
+    std::vector<int> var(nprob, 0), sck(nprob, 1);
+    ctx->batched_buckets.clear();
+    // the descriptors reach the device here for the first time: kb_guess and
+    // every later kernel read them
+    if ((rc = apply_choices(ctx, p, tabs, ch, var, sck, nullptr)) != SQD_OK) return fail(rc);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (double sc : cand) {
-        if ((rc = set_groups(ctx, p, tabs, sc)) != SQD_OK) return fail(rc);
-        kb_guess<<<nprob, 256, 0, ctx->stream>>>(p.D, p.S);
-        SQD_LAUNCHED(ctx);
-        cudaEventRecord(e0, ctx->stream);
-        if ((rc = launch_sigma_stages(ctx, p)) != SQD_OK) return fail(rc);
-        cudaEventRecord(e1, ctx->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess)
-            return fail(sqd_fail(ctx, SQD_ECUDA, "sigma stage failed: %s",
-                                 cudaGetErrorString(cudaGetLastError())));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = sc;
+    kb_guess<<<nprob, 256, 0, ctx->stream>>>(p.D, p.S);
+    SQD_LAUNCHED(ctx);
+    int fk = -1;  // a fixed tile instead of tuning (sqd_batched_set_tile)
+    for (int k = 0; k < AB_NSCALE; k++)
+        if (ctx->batched_force_ept && kAbScales[k] == ctx->batched_force_scale) fk = k;
+    for (int q = 0; q < nbk; q++) {
+        const int lo = q * nprob / nbk, hi = (q + 1) * nprob / nbk;
+        if (fk >= 0) {
+            const int fv = ctx->batched_force_ept == AB_EPT_WIDE ? 0 : 1;
+            for (int r = lo; r < hi; r++) {
+                var[order[r]] = fv;
+                sck[order[r]] = fk;
+            }
+            sqd_ctx::bucket_choice bc;
+            bc.max_det = p.hdesc[order[hi - 1]].N;
+            bc.scale = kAbScales[fk];
+            bc.entries_per_thread = ctx->batched_force_ept;
+            ctx->batched_buckets.push_back(bc);
+            continue;
         }
+        std::vector<char> on(nprob, 0);
+        for (int r = std::max(lo, hi - 4); r < hi; r++) on[order[r]] = 1;
+        double best_ms = INFINITY;
+        int bv = 0, bs = 1;
+        for (int v = 0; v < 2; v++) {
+            for (int k = 0; k < AB_NSCALE; k++) {
+                for (int r = lo; r < hi; r++) {
+                    var[order[r]] = v;
+                    sck[order[r]] = k;
+                }
+                if ((rc = apply_choices(ctx, p, tabs, ch, var, sck, &on)) != SQD_OK)
+                    return fail(rc);
+                float best_rep = INFINITY;
+                for (int rep = 0; rep < 2; rep++) {
+                    kb_zero_counters<<<1, 32, 0, ctx->stream>>>(p.counters, 5);
+                    SQD_LAUNCHED(ctx);
+                    cudaEventRecord(e0, ctx->stream);
+                    if ((rc = launch_ab_stage(ctx, p)) != SQD_OK) return fail(rc);
+                    cudaEventRecord(e1, ctx->stream);
+                    if (cudaEventSynchronize(e1) != cudaSuccess)
+                        return fail(sqd_fail(ctx, SQD_ECUDA, "sigma stage failed: %s",
+                                             cudaGetErrorString(cudaGetLastError())));
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    best_rep = std::min(best_rep, ms);
+                }
+                if (best_rep < best_ms) {
+                    best_ms = best_rep;
+                    bv = v;
+                    bs = k;
+                }
+            }
+        }
+        for (int r = lo; r < hi; r++) {
+            var[order[r]] = bv;
+            sck[order[r]] = bs;
+        }
+        sqd_ctx::bucket_choice bc;
+        bc.max_det = p.hdesc[order[hi - 1]].N;
+        bc.scale = kAbScales[bs];
+        bc.entries_per_thread = bv == 0 ? AB_EPT_WIDE : AB_EPT;
+        ctx->batched_buckets.push_back(bc);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->batched_group_scale = best;
-    if ((rc = set_groups(ctx, p, tabs, best)) != SQD_OK) return fail(rc);
+    ctx->batched_group_scale = kAbScales[sck[order[nprob - 1]]];
+    if ((rc = apply_choices(ctx, p, tabs, ch, var, sck, nullptr)) != SQD_OK) return fail(rc);
+    // the tuning sigma wrote W[0]: the guess and its sigma start afresh below
 
     // --- initial guess, its sigma and G[0][0] ------------------------------
-    prof_begin(ctx, PROF_DAVIDSON);
+    prof_begin(ctx, PROF_BATCHED);
     kb_guess<<<nprob, 256, 0, ctx->stream>>>(p.D, p.S);
     SQD_LAUNCHED(ctx);
     if ((rc = launch_sigma_stages(ctx, p)) != SQD_OK) return fail(rc);
@@ -907,12 +1300,28 @@ int davidson_batched_impl(sqd_ctx *ctx, int nprob, sqd_tables *const *tables,
     cudaGraphDestroy(graph);
     cudaStreamDestroy(cap);
     prof_end(ctx, 0.0, 0.0);
+    if (p.stamps) {
+        double acc[13];
+        if (cudaMemcpyAsync(acc, p.stamps, sizeof(acc), cudaMemcpyDeviceToHost, ctx->stream) ==
+                cudaSuccess &&
+            cudaStreamSynchronize(ctx->stream) == cudaSuccess) {
+            const int cls[3] = {PROF_B_SIGMA, PROF_B_VECTOR, PROF_B_EIGH};
+            for (int q = 0; q < 3; q++) {
+                ctx->cls_ms[cls[q]] += acc[q] * 1e-6;
+                ctx->cls_flops[cls[q]] += acc[3 + q];
+                ctx->cls_bytes[cls[q]] += acc[6 + q];
+                ctx->cls_launches[cls[q]] += (int64_t)acc[9 + q];
+            }
+        }
+    }
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess)
         return fail(sqd_fail(ctx, SQD_ECUDA, "batched Davidson failed: %s",
                              cudaGetErrorString(ce)));
 
     // --- outputs -----------------------------------------------------------
+    kb_form_x<<<(unsigned)p.tot_vec, BV_THREADS, 0, ctx->stream>>>(p.D, p.S, p.pre_vec, nprob);
+    SQD_LAUNCHED(ctx);
     std::vector<bstate> hs(nprob);
     if (cudaMemcpy(hs.data(), p.S, sizeof(bstate) * nprob, cudaMemcpyDeviceToHost) != cudaSuccess)
         return fail(sqd_fail(ctx, SQD_ECUDA, "state copy failed"));

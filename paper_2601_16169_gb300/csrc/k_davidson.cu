@@ -112,15 +112,18 @@ template <int JN>
 __global__ void __launch_bounds__(256) k_combine(const double *__restrict__ A, int64_t lda, int m,
                                                  const double *__restrict__ Yj, int ldy,
                                                  double *__restrict__ oj, int64_t ldo, int64_t n,
-                                                 int sub) {
+                                                 int sub, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;  // a pass the device decided to skip
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x)
         combine_group<JN>(A, lda, m, Yj, ldy, oj, ldo, p, sub);
 }
 
-// out_j (-)= sum_i A_i Y_ij for j < k, one launch per group of 8 outputs
+// out_j (-)= sum_i A_i Y_ij for j < k, one launch per group of 8 outputs;
+// with gate, only if *gate != 0 (read on the device)
 static int combine_launch(sqd_ctx *ctx, const double *A, int64_t lda, int m, const double *Y,
-                          int ldy, int k, double *out, int64_t ldo, int64_t n, int sub) {
+                          int ldy, int k, double *out, int64_t ldo, int64_t n, int sub,
+                          const int *gate = nullptr) {
     if (k == 0 || n == 0) return SQD_OK;
     unsigned g = grid_1d(n, 256);
     if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
@@ -129,14 +132,14 @@ static int combine_launch(sqd_ctx *ctx, const double *A, int64_t lda, int m, con
         double *oj = out + (int64_t)j0 * ldo;
         cudaStream_t st = ctx->stream;
         switch (min(8, k - j0)) {
-            case 1: k_combine<1><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub); break;
-            case 2: k_combine<2><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub); break;
-            case 3: k_combine<3><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub); break;
-            case 4: k_combine<4><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub); break;
-            case 5: k_combine<5><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub); break;
-            case 6: k_combine<6><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub); break;
-            case 7: k_combine<7><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub); break;
-            default: k_combine<8><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub); break;
+            case 1: k_combine<1><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub, gate); break;
+            case 2: k_combine<2><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub, gate); break;
+            case 3: k_combine<3><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub, gate); break;
+            case 4: k_combine<4><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub, gate); break;
+            case 5: k_combine<5><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub, gate); break;
+            case 6: k_combine<6><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub, gate); break;
+            case 7: k_combine<7><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub, gate); break;
+            default: k_combine<8><<<g, 256, 0, st>>>(A, lda, m, Yj, ldy, oj, ldo, n, sub, gate); break;
         }
         SQD_LAUNCHED(ctx);
     }
@@ -157,9 +160,9 @@ int launch_gemv_sub(sqd_ctx *ctx, const double *A, int64_t lda, int m, const dou
 
 // out_j[n] -= sum_i A_i[n] Y[i + j*ldy], j < k: the update of block Gram-Schmidt
 int launch_combine_sub(sqd_ctx *ctx, const double *A, int64_t lda, int m, const double *Y,
-                       int ldy, int k, double *out, int64_t ldo, int64_t n) {
+                       int ldy, int k, double *out, int64_t ldo, int64_t n, const int *gate) {
     if (m == 0) return SQD_OK;
-    return combine_launch(ctx, A, lda, m, Y, ldy, k, out, ldo, n, 1);
+    return combine_launch(ctx, A, lda, m, Y, ldy, k, out, ldo, n, 1, gate);
 }
 
 // ------------------------------------------------- block dot products ---
@@ -191,7 +194,8 @@ static int block_dot_kc(int m, int b) {
 __global__ void __launch_bounds__(RED_THREADS)
     k_block_dot_partial(const double *__restrict__ A, int64_t lda, int m,
                         const double *__restrict__ X, int64_t ldx, int b, int64_t n, int kc,
-                        double *__restrict__ partial) {
+                        double *__restrict__ partial, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;  // a pass the device decided to skip
     extern __shared__ double bd_sh[];
     const int ld = kc + 1;
     double *As = bd_sh, *Xs = bd_sh + (size_t)m * ld;
@@ -254,7 +258,8 @@ __global__ void __launch_bounds__(RED_THREADS)
 }
 
 __global__ void k_block_dot_final(const double *__restrict__ partial, int nblk, int m, int b,
-                                  double *__restrict__ out, int ldo) {
+                                  double *__restrict__ out, int ldo, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     const int mb = m * b;
     if (o >= mb) return;
@@ -265,7 +270,7 @@ __global__ void k_block_dot_final(const double *__restrict__ partial, int nblk, 
 
 int launch_block_dot(sqd_ctx *ctx, const double *A, int64_t lda, int m, const double *X,
                      int64_t ldx, int b, int64_t n, double *partial, int nblk, double *out,
-                     int ldo) {
+                     int ldo, const int *gate) {
     if (m == 0 || b == 0) return SQD_OK;
     if (m > JAC_MAX || b > BD_MAXB || m * b > RED_THREADS * BD_OUT)
         return sqd_fail(ctx, SQD_EINVAL, "block dot of %d x %d vectors out of range", m, b);
@@ -274,9 +279,35 @@ int launch_block_dot(sqd_ctx *ctx, const double *A, int64_t lda, int m, const do
     if (shm < sizeof(double) * RED_THREADS) shm = sizeof(double) * RED_THREADS;
     // at most (112 + 32) rows x 33 columns = 38 KB: within the default 48 KB
     k_block_dot_partial<<<nblk, RED_THREADS, shm, ctx->stream>>>(A, lda, m, X, ldx, b, n, kc,
-                                                                  partial);
+                                                                  partial, gate);
     SQD_LAUNCHED(ctx);
-    k_block_dot_final<<<(m * b + 127) / 128, 128, 0, ctx->stream>>>(partial, nblk, m, b, out, ldo);
+    k_block_dot_final<<<(m * b + 127) / 128, 128, 0, ctx->stream>>>(partial, nblk, m, b, out, ldo,
+                                                                    gate);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// Daniel-Gragg-Kaufman-Stewart test on the device: *flag = 1 if some vector
+// of the block lost more than `loss` of its squared norm in the first
+// Gram-Schmidt pass (|P_j|^2 > loss |t_j|^2, V orthonormal), else 0; the
+// second pass is gated on it.  One block.
+__global__ void k_dgks_flag(const double *__restrict__ P, int ldp, int m, int b,
+                            const double *__restrict__ tn2, double loss, int *__restrict__ flag) {
+    __shared__ int again;
+    if (threadIdx.x == 0) again = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < b; j += blockDim.x) {
+        double p2 = 0.0;
+        for (int i = 0; i < m; i++) p2 = fma(P[i + (int64_t)j * ldp], P[i + (int64_t)j * ldp], p2);
+        if (!(p2 <= loss * tn2[j])) atomicOr(&again, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *flag = again;
+}
+
+int launch_dgks_flag(sqd_ctx *ctx, const double *P, int ldp, int m, int b, const double *tn2,
+                     double loss, int *flag) {
+    k_dgks_flag<<<1, 32, 0, ctx->stream>>>(P, ldp, m, b, tn2, loss, flag);
     SQD_LAUNCHED(ctx);
     return SQD_OK;
 }
@@ -436,7 +467,8 @@ int launch_project_g(sqd_ctx *ctx, double *G, int ldg, int m, const double *Z, i
     return SQD_OK;
 }
 
-// T = R / (theta - diag), |denominator| clamped to floor_ (sign kept, + for 0);
+// T = R / (theta - diag), |denominator| clamped to floor_ (sign kept, + for 0;
+// the reciprocal by precond_recip);
 // with partial != NULL also per-block partial sums of T^2
 __global__ void __launch_bounds__(RED_THREADS)
     k_precondition(const double *__restrict__ R, const double *__restrict__ diag, double theta,
@@ -445,9 +477,7 @@ __global__ void __launch_bounds__(RED_THREADS)
     double ss = 0.0;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
-        double d = theta - diag[p];
-        if (fabs(d) < floor_) d = (d < 0.0) ? -floor_ : floor_;
-        const double t = R[p] / d;
+        const double t = R[p] * precond_recip(theta - diag[p], floor_);
         T[p] = t;
         ss = fma(t, t, ss);
     }
@@ -782,5 +812,279 @@ int launch_fix_phase(sqd_ctx *ctx, double *X, int64_t ld, int k, int64_t n, doub
         SQD_LAUNCHED(ctx);
         SQD_TRY(launch_scale(ctx, x, n, sg, 0));
     }
+    return SQD_OK;
+}
+
+// ----------------------------------------------- one-vector fused passes --
+// The one-root Davidson (a block of one new vector, m <= 16 basis vectors)
+// is bound by HBM at large N: every pass over a basis vector costs 8 N bytes.
+// These kernels cut the passes of an iteration from about 7 m + 16 vectors
+// to 5 m + 8 by fusing what reads the same vectors:
+//   k_ritz_prec_dot : x = V y, r = W y - theta x, t = r / (theta - H_II) and
+//                     the projections V_i . t of the first Gram-Schmidt pass,
+//                     with |r|^2 and |t|^2 (the Ritz vector is not stored);
+//   k_gs_update_dot : t' = t - V p (first update) with V_i . t' (second pass
+//                     projections) and |t'|^2;
+//   k_gs_update_scale: t'' = (t' - V p') * s (second update and the
+//                     normalisation; s = 1 / |t''| from |t''|^2 =
+//                     |t'|^2 - |p'|^2, Pythagoras, V orthonormal).
+// y, theta and p are read from device memory, so no host round trip sits
+// between the eigensolve and the correction.  Per-block partials are summed
+// in a fixed order by k_sum_partials.
+
+// Each kernel is instantiated for the exact basis size MB (1..16): every
+// load of an element's MB basis values is issued before its arithmetic, with
+// no predicated-off slots, and the two Ritz sums run as two chains each.
+template <int MB>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_ritz_prec_dot(const double *__restrict__ V, const double *__restrict__ W, int64_t ld,
+                    const double *__restrict__ y, const double *__restrict__ theta_p,
+                    const double *__restrict__ diag, double floor_, int64_t n,
+                    double *__restrict__ T, double *__restrict__ partial) {
+    __shared__ double red[(RED_THREADS / 32) * (MB + 2)];
+    __shared__ double ys[MB];
+    if (threadIdx.x < MB) ys[threadIdx.x] = y[threadIdx.x];
+    __syncthreads();
+    const double th = *theta_p;
+    double acc[MB];
+#pragma unroll
+    for (int i = 0; i < MB; i++) acc[i] = 0.0;
+    double s_r = 0.0, s_t = 0.0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double vv[MB], ww[MB];
+#pragma unroll
+        for (int i = 0; i < MB; i++) {
+            vv[i] = V[(int64_t)i * ld + p];
+            ww[i] = W[(int64_t)i * ld + p];
+        }
+        const double dg = diag[p];
+        double x0 = 0.0, x1 = 0.0, w0 = 0.0, w1 = 0.0;
+#pragma unroll
+        for (int i = 0; i < MB; i += 2) {
+            x0 = fma(vv[i], ys[i], x0);
+            w0 = fma(ww[i], ys[i], w0);
+            if (i + 1 < MB) {
+                x1 = fma(vv[i + 1], ys[i + 1], x1);
+                w1 = fma(ww[i + 1], ys[i + 1], w1);
+            }
+        }
+        const double r = fma(-th, x0 + x1, w0 + w1);
+        const double t = r * precond_recip(th - dg, floor_);
+        T[p] = t;
+        s_r = fma(r, r, s_r);
+        s_t = fma(t, t, s_t);
+#pragma unroll
+        for (int i = 0; i < MB; i++) acc[i] = fma(vv[i], t, acc[i]);
+    }
+    double vals[MB + 2];
+#pragma unroll
+    for (int i = 0; i < MB; i++) vals[i] = acc[i];
+    vals[MB] = s_r;
+    vals[MB + 1] = s_t;
+    int i;
+    double v;
+    if (block_sums<MB + 2>(vals, red, &i, &v)) partial[(int64_t)blockIdx.x * (MB + 2) + i] = v;
+}
+
+template <int MB>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_gs_update_dot(const double *__restrict__ V, int64_t ld, const double *__restrict__ P,
+                    double *__restrict__ T, int64_t n, double *__restrict__ partial) {
+    __shared__ double red[(RED_THREADS / 32) * (MB + 1)];
+    __shared__ double ps[MB];
+    if (threadIdx.x < MB) ps[threadIdx.x] = P[threadIdx.x];
+    __syncthreads();
+    double acc[MB];
+#pragma unroll
+    for (int i = 0; i < MB; i++) acc[i] = 0.0;
+    double s_t = 0.0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double vv[MB];
+#pragma unroll
+        for (int i = 0; i < MB; i++) vv[i] = V[(int64_t)i * ld + p];
+        const double t0 = T[p];
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int i = 0; i < MB; i += 2) {
+            s0 = fma(vv[i], ps[i], s0);
+            if (i + 1 < MB) s1 = fma(vv[i + 1], ps[i + 1], s1);
+        }
+        const double t = t0 - (s0 + s1);
+        T[p] = t;
+        s_t = fma(t, t, s_t);
+#pragma unroll
+        for (int i = 0; i < MB; i++) acc[i] = fma(vv[i], t, acc[i]);
+    }
+    double vals[MB + 1];
+#pragma unroll
+    for (int i = 0; i < MB; i++) vals[i] = acc[i];
+    vals[MB] = s_t;
+    int i;
+    double v;
+    if (block_sums<MB + 1>(vals, red, &i, &v)) partial[(int64_t)blockIdx.x * (MB + 1) + i] = v;
+}
+
+template <int MB>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_gs_update_scale(const double *__restrict__ V, int64_t ld, const double *__restrict__ P,
+                      double scale, double *__restrict__ T, int64_t n) {
+    __shared__ double ps[MB];
+    if (threadIdx.x < MB) ps[threadIdx.x] = P[threadIdx.x];
+    __syncthreads();
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double vv[MB];
+#pragma unroll
+        for (int i = 0; i < MB; i++) vv[i] = V[(int64_t)i * ld + p];
+        const double t0 = T[p];
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int i = 0; i < MB; i += 2) {
+            s0 = fma(vv[i], ps[i], s0);
+            if (i + 1 < MB) s1 = fma(vv[i + 1], ps[i + 1], s1);
+        }
+        T[p] = (t0 - (s0 + s1)) * scale;
+    }
+}
+
+// compile-time basis size for the dispatch below
+template <int N>
+struct mb_int {
+    static constexpr int value = N;
+};
+// call f(mb_int<m>{}) for m in [1, 16]
+#define MB_CASE(N, f) \
+    case N:           \
+        f(mb_int<N>{}); \
+        break;
+#define MB_DISPATCH(m, f)                                                                     \
+    switch (m) {                                                                              \
+        MB_CASE(1, f) MB_CASE(2, f) MB_CASE(3, f) MB_CASE(4, f) MB_CASE(5, f) MB_CASE(6, f)   \
+        MB_CASE(7, f) MB_CASE(8, f) MB_CASE(9, f) MB_CASE(10, f) MB_CASE(11, f)              \
+        MB_CASE(12, f) MB_CASE(13, f) MB_CASE(14, f) MB_CASE(15, f)                          \
+        default: f(mb_int<16>{}); break;                                                      \
+    }
+
+// out[i] = sum over blocks b of partial[b * stride + i], i < cnt (fixed order)
+__global__ void k_sum_partials(const double *__restrict__ partial, int nblk, int stride,
+                               int cnt, double *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; b++) s += partial[(int64_t)b * stride + i];
+    out[i] = s;
+}
+
+// in place: A_j[n] = sum_i A_i[n] Z[i + j*ldz] for j < r <= 4 (every element
+// is read by one thread before it writes, so the in-place update is safe)
+template <int R>
+__global__ void __launch_bounds__(256) k_combine_inplace(double *A, int64_t lda, int m,
+                                                         const double *__restrict__ Z, int ldz,
+                                                         int64_t n) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double acc[R];
+#pragma unroll
+        for (int j = 0; j < R; j++) acc[j] = 0.0;
+        for (int i = 0; i < m; i++) {
+            const double a = A[(int64_t)i * lda + p];
+#pragma unroll
+            for (int j = 0; j < R; j++) acc[j] = fma(a, __ldg(Z + i + (int64_t)j * ldz), acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < R; j++) A[(int64_t)j * lda + p] = acc[j];
+    }
+}
+
+// P_new[j] = sum_i Z[i + j*ldz] P_old[i], j < r (the projections of a vector
+// on the restarted basis V Z); one block
+__global__ void k_project_coeffs(const double *__restrict__ Z, int ldz, int m, int r,
+                                 const double *__restrict__ Pold, double *__restrict__ Pnew) {
+    const int j = threadIdx.x;
+    if (j >= r) return;
+    double s = 0.0;
+    for (int i = 0; i < m; i++) s = fma(Z[i + (int64_t)j * ldz], Pold[i], s);
+    Pnew[j] = s;
+}
+
+int fused_md(int M) { return M <= 16 ? 16 : 0; }
+
+// sums[0..m) = V^T t, sums[m] = |r|^2, sums[m+1] = |t|^2; partial: nblk*(m+2)
+int launch_ritz_prec_dot(sqd_ctx *ctx, int MD, const double *V, const double *W, int64_t ld,
+                         int m, const double *y, const double *theta, const double *diag,
+                         double floor_, int64_t n, double *T, double *partial, int nblk,
+                         double *sums) {
+    if (m < 1 || m > MD || MD != 16)
+        return sqd_fail(ctx, SQD_EINVAL, "fused Ritz pass: m = %d out of range", m);
+    cudaStream_t st = ctx->stream;
+    auto go = [&](auto mb) {
+        constexpr int MB = decltype(mb)::value;
+        k_ritz_prec_dot<MB><<<nblk, RED_THREADS, 0, st>>>(V, W, ld, y, theta, diag, floor_, n, T,
+                                                          partial);
+    };
+    MB_DISPATCH(m, go);
+    SQD_LAUNCHED(ctx);
+    k_sum_partials<<<1, 64, 0, st>>>(partial, nblk, m + 2, m + 2, sums);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// T -= V P; sums[0..m) = V^T T (after), sums[m] = |T|^2 (after)
+int launch_gs_update_dot(sqd_ctx *ctx, int MD, const double *V, int64_t ld, int m,
+                         const double *P, double *T, int64_t n, double *partial, int nblk,
+                         double *sums) {
+    if (m < 1 || m > MD || MD != 16)
+        return sqd_fail(ctx, SQD_EINVAL, "fused Gram-Schmidt pass: m = %d out of range", m);
+    cudaStream_t st = ctx->stream;
+    auto go = [&](auto mb) {
+        constexpr int MB = decltype(mb)::value;
+        k_gs_update_dot<MB><<<nblk, RED_THREADS, 0, st>>>(V, ld, P, T, n, partial);
+    };
+    MB_DISPATCH(m, go);
+    SQD_LAUNCHED(ctx);
+    k_sum_partials<<<1, 64, 0, st>>>(partial, nblk, m + 1, m + 1, sums);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// T = (T - V P) * scale
+int launch_gs_update_scale(sqd_ctx *ctx, int MD, const double *V, int64_t ld, int m,
+                           const double *P, double scale, double *T, int64_t n, int nblk) {
+    if (m < 1 || m > MD || MD != 16)
+        return sqd_fail(ctx, SQD_EINVAL, "fused Gram-Schmidt pass: m = %d out of range", m);
+    cudaStream_t st = ctx->stream;
+    auto go = [&](auto mb) {
+        constexpr int MB = decltype(mb)::value;
+        k_gs_update_scale<MB><<<nblk, RED_THREADS, 0, st>>>(V, ld, P, scale, T, n);
+    };
+    MB_DISPATCH(m, go);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+int launch_combine_inplace(sqd_ctx *ctx, double *A, int64_t lda, int m, const double *Z, int ldz,
+                           int r, int64_t n) {
+    if (r < 1 || r > 4 || r > m)
+        return sqd_fail(ctx, SQD_EINVAL, "in-place combination of %d vectors", r);
+    unsigned g = grid_1d(n, 256);
+    if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
+    cudaStream_t st = ctx->stream;
+    switch (r) {
+        case 1: k_combine_inplace<1><<<g, 256, 0, st>>>(A, lda, m, Z, ldz, n); break;
+        case 2: k_combine_inplace<2><<<g, 256, 0, st>>>(A, lda, m, Z, ldz, n); break;
+        case 3: k_combine_inplace<3><<<g, 256, 0, st>>>(A, lda, m, Z, ldz, n); break;
+        default: k_combine_inplace<4><<<g, 256, 0, st>>>(A, lda, m, Z, ldz, n); break;
+    }
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+int launch_project_coeffs(sqd_ctx *ctx, const double *Z, int ldz, int m, int r,
+                          const double *Pold, double *Pnew) {
+    if (r < 1 || r > 128) return sqd_fail(ctx, SQD_EINVAL, "bad restart size %d", r);
+    k_project_coeffs<<<1, 128, 0, ctx->stream>>>(Z, ldz, m, r, Pold, Pnew);
+    SQD_LAUNCHED(ctx);
     return SQD_OK;
 }

@@ -10,6 +10,11 @@
 #include "../../include/sqd.h"
 
 // Kernel classes for the measurement counters (sqd_profile_*).
+// largest Davidson subspace (the one-block Jacobi eigensolver's limit);
+// nroots is limited to a quarter of it (the restart needs 4 nroots vectors)
+#define SQD_MAX_SUBSPACE 112
+#define SQD_MAX_ROOTS (SQD_MAX_SUBSPACE / 4)
+
 enum prof_class {
     PROF_SAME_ALPHA = 0,  // k_same_spin on C with the alpha tables (+ diagonal)
     PROF_SAME_BETA,       // k_same_spin on C^T with the beta tables
@@ -22,6 +27,10 @@ enum prof_class {
     PROF_STORED,          // stored-H sparse matrix-vector product
     PROF_ORTHO,           // Davidson Gram-Schmidt and projected-matrix columns
     PROF_EIGH,            // Davidson Rayleigh-Ritz eigensolver
+    PROF_BATCHED,         // a whole batched solve (setup, tuning, loop, outputs)
+    PROF_B_SIGMA,         // batched loop: sigma stages (device-timed per iteration)
+    PROF_B_VECTOR,        // batched loop: Ritz, restart, correction, Gram-Schmidt, G columns
+    PROF_B_EIGH,          // batched loop: the per-subspace Jacobi eigensolves
     PROF_NCLASS
 };
 
@@ -45,7 +54,15 @@ struct sqd_ctx {
     double cls_flops[PROF_NCLASS] = {0};
     double cls_bytes[PROF_NCLASS] = {0};
     double cls_ms[PROF_NCLASS] = {0};
-    double batched_group_scale = 0.0;    // last autotuned alpha-group scale
+    double batched_group_scale = 0.0;    // last autotuned alpha-group scale (largest bucket)
+    struct bucket_choice {
+        int64_t max_det;         // largest subspace (determinants) of the bucket
+        double scale;            // alpha-row group scale
+        int entries_per_thread;  // paired-singles tile: 16 (wide, persistent) or 8 (grid)
+    };
+    std::vector<bucket_choice> batched_buckets;  // last batched solve's per-bucket tiles
+    int batched_force_ept = 0;       // fixed paired-singles tile (8 or 16), 0 = autotune
+    double batched_force_scale = 0;  // fixed alpha-group scale with it
     int batched_device_loop = 0;         // 1: last batched solve looped inside one graph
 };
 
@@ -221,11 +238,14 @@ int launch_gemv_sub(sqd_ctx *, const double *A, int64_t lda, int m, const double
 int launch_combine(sqd_ctx *, const double *A, int64_t lda, int m, const double *Y,
                    int ldy, int k, double *out, int64_t ldo, int64_t n);
 int launch_combine_sub(sqd_ctx *, const double *A, int64_t lda, int m, const double *Y,
-                       int ldy, int k, double *out, int64_t ldo, int64_t n);
+                       int ldy, int k, double *out, int64_t ldo, int64_t n,
+                       const int *gate = nullptr);
+int launch_dgks_flag(sqd_ctx *, const double *P, int ldp, int m, int b, const double *tn2,
+                     double loss, int *flag);
 int block_dot_blocks(const sqd_ctx *, int64_t n);
 int launch_block_dot(sqd_ctx *, const double *A, int64_t lda, int m, const double *X,
                      int64_t ldx, int b, int64_t n, double *partial, int nblk, double *out,
-                     int ldo);
+                     int ldo, const int *gate = nullptr);
 int launch_ritz_block(sqd_ctx *, const double *V, const double *W, int64_t ld, int m,
                       const double *Y, const double *theta, const int *sel, int ks, double *X,
                       double *R, int64_t n, double *partial, int nblk, double *rnorm2);
@@ -247,6 +267,19 @@ int launch_fix_phase(sqd_ctx *, double *X, int64_t ld, int k, int64_t n, double 
 int launch_gdk_basis(sqd_ctx *, const double *Y, int m, int m2, const double *P, int mp, int k,
                      int ldp, double *Z, int ldz, int *r_dev);
 int launch_identity_cols(sqd_ctx *, double *Y, int r, int k, int ld);
+// one-root Davidson: fused passes (MD = fused_md(M): 16 or 32, 0 = unavailable)
+int fused_md(int M);
+int launch_ritz_prec_dot(sqd_ctx *, int MD, const double *V, const double *W, int64_t ld, int m,
+                         const double *y, const double *theta, const double *diag, double floor_,
+                         int64_t n, double *T, double *partial, int nblk, double *sums);
+int launch_gs_update_dot(sqd_ctx *, int MD, const double *V, int64_t ld, int m, const double *P,
+                         double *T, int64_t n, double *partial, int nblk, double *sums);
+int launch_gs_update_scale(sqd_ctx *, int MD, const double *V, int64_t ld, int m,
+                           const double *P, double scale, double *T, int64_t n, int nblk);
+int launch_combine_inplace(sqd_ctx *, double *A, int64_t lda, int m, const double *Z, int ldz,
+                           int r, int64_t n);
+int launch_project_coeffs(sqd_ctx *, const double *Z, int ldz, int m, int r, const double *Pold,
+                          double *Pnew);
 
 // double-float sigma
 int df_prepare(sqd_ctx *ctx, sqd_tables *t);
@@ -267,6 +300,9 @@ int stored_build(sqd_ctx *ctx, sqd_tables *t, int64_t max_bytes, int64_t *nnz_ou
 int stored_sigma(sqd_ctx *ctx, const sqd_tables *t, const double *C, double *S, int nvec);
 
 // batched
+// algorithmic FP64 flops of one sigma of one vector: alpha side (+ diagonal),
+// beta side, alpha-beta paired singles
+void sigma_work(const sqd_tables *t, double *f_a, double *f_b, double *f_ab);
 int davidson_batched_impl(sqd_ctx *ctx, int nprob, sqd_tables *const *tables,
                           const sqd_options *o, double *h_energies, double *const *d_C,
                           int *h_iters, int *h_status);

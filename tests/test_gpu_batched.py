@@ -37,8 +37,13 @@ def _compare(sqd, ctx, subs, tol_r=1e-8):
     e, Cs, it, st, rc = sqd.davidson_batched(ctx, tabs, tol_residual=tol_r, tol_energy=1e-10)
     assert rc == 0 and np.all(st == 0)
     scale, device_loop = sqd.batched_tuning(ctx, with_loop=True)
-    assert 0.0 < scale <= 1.0
+    assert scale in (0.5, 1.0, 2.0)
     assert device_loop  # the iteration loop ran inside one graph
+    bk = sqd.batched_tuning_buckets(ctx)
+    assert 1 <= len(bk) <= min(4, len(subs))
+    assert all(b["entries_per_thread"] in (8, 16) and b["scale"] in (0.5, 1.0, 2.0) for b in bk)
+    assert [b["max_det"] for b in bk] == sorted(b["max_det"] for b in bk)
+    assert bk[-1]["max_det"] == max(w.ndet for w in subs)
     for b, t in enumerate(tabs):
         e1, X1, _, _, _ = sqd.davidson(ctx, t, nroots=1, tol_residual=tol_r, tol_energy=1e-10)
         # the two solvers differ only in summation order and restart path
@@ -81,3 +86,33 @@ def test_batched_config3_sample(sqd, ctx):
     # a sample of the 64-subspace workload (its first 6 subspaces, 4e4-9e6 dets)
     subs = si.batched_workload(nbatch=64)[:6]
     _compare(sqd, ctx, subs, tol_r=1e-7)
+
+
+@pytest.mark.parametrize("tile", [(16, 1.0), (8, 0.5), (8, 2.0)])
+def test_batched_large_subspaces_oracle_residuals(sqd, ctx, tile):
+    # subspaces of 1100-1500 strings (1.2e6-2.3e6 determinants, 23000-33000
+    # single entries per spin) fill several 4096-entry and 2048-entry
+    # paired-singles chunks; each tile is forced in turn, and the batched
+    # ground states are pinned to the oracle: the residual of the returned
+    # vector, formed with the oracle sigma over every row, is within the
+    # requested tolerance (Weinstein: an eigenvalue within |r| of E)
+    subs = si.batched_workload(nbatch=3, sizes=[1500, 1100, 300])
+    tabs = [_tables(sqd, ctx, w) for w in subs]
+    for t in tabs[:2]:
+        assert t.info()["nnz1_alpha"] >= 2 * 4096
+    sqd.batched_set_tile(ctx, *tile)
+    try:
+        e, Cs, it, st, rc = sqd.davidson_batched(ctx, tabs, tol_residual=1e-7, tol_energy=1e-10)
+    finally:
+        sqd.batched_set_tile(ctx, 0)
+    assert rc == 0 and np.all(st == 0)
+    bk = sqd.batched_tuning_buckets(ctx)
+    assert all(b["entries_per_thread"] == tile[0] and b["scale"] == tile[1] for b in bk)
+    for b, w in enumerate(subs):
+        x = Cs[b].cpu().numpy().reshape(-1)
+        S = oracle.sigma(w.norb, w.h, w.V, 0.0, w.strings_a, w.strings_b, x)
+        assert abs(np.linalg.norm(x) - 1.0) <= 1e-12
+        assert np.linalg.norm(S - e[b] * x) <= 1e-7 * (1 + 1e-6), b
+        assert abs(float(x @ S) - e[b]) <= 1e-11 * abs(e[b])
+    for t in tabs:
+        t.close()

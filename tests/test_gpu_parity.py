@@ -414,3 +414,18 @@ def test_single_determinant_space(sqd, ctx):
     assert abs(e[0] - oracle.diag(6, h, V, 0.5, s, s)[0]) <= 1e-13
     assert float(X.abs().sum()) == 1.0
     t.close()
+
+
+def test_sigma_run_to_run_spread(sqd, ctx):
+    # the paired-singles term adds its entry sums into sigma with FP64
+    # atomics, so the summation order (not the terms) varies between runs:
+    # two products of the same vector agree to a few units of rounding
+    w = si.workload("adjoint29")
+    t = make_tables(sqd, ctx, w.norb, w.strings_a, 5, w.strings_b, 5, w.h, w.V)
+    C = dev_f64(si.random_vectors(1, w.ndet, 31).reshape(w.strings_a.size, -1))
+    S1 = sqd.sigma(ctx, t, C)
+    S2 = sqd.sigma(ctx, t, C)
+    d = float((S1 - S2).abs().max())
+    assert d <= 1e-14 * float(S1.abs().max())
+    assert float((S1 - S2).norm()) <= 1e-14 * float(S1.norm())
+    t.close()

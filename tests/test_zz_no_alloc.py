@@ -47,6 +47,24 @@ def test_noalloc_matches_build_strings_twice():
     ctx.close()
 
 
+def test_noalloc_in_place_twice():
+    # the output buffer may be the input buffer, as for sqd_build_strings:
+    # the raw strings reach the scratch array before the output is written
+    import paper_2601_16169_gb300 as sqd
+    torch.cuda.set_device(0)
+    ctx = sqd.Context(0)
+    for raw, norb, ne in _cases():
+        d_raw = torch.tensor(raw.view(np.int64), device="cuda")
+        ref = sqd.build_strings(ctx, d_raw, norb, ne).cpu()
+        buf = d_raw.clone()
+        for _ in range(2):  # the second call filters the first call's output in place
+            n = sqd.build_strings_noalloc(ctx, buf, norb, ne, buf)
+            assert n == ref.numel()
+            assert torch.equal(buf[:n].cpu(), ref)
+            buf = buf[:n].clone() if n else buf[:0]
+    ctx.close()
+
+
 def test_noalloc_rejects_inputs_over_its_limit():
     import paper_2601_16169_gb300 as sqd
     ctx = sqd.Context(0)
