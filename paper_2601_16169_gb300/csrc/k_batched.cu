@@ -164,9 +164,14 @@ __global__ void __launch_bounds__(AB_THREADS, KB_AB_MINB) kb_alpha_beta(const bd
 
 // the same stage as a plain grid over the items of the subspaces tuned to
 // it: the single-problem kernel's tile (standard chunks of AB_ECAP entries,
-// AB_EPT entries per thread, AB_MINB blocks per SM) with the subspace looked
+// AB_EPT entries per thread) with the subspace looked
 // up from the block index; blocks of subspaces without a new vector exit
-__global__ void __launch_bounds__(AB_THREADS, AB_MINB)
+// 3 blocks per SM: the subspace lookup adds registers to the single-problem
+// tile, which spills at 4
+#ifndef KB_GRID_MINB
+#define KB_GRID_MINB 3
+#endif
+__global__ void __launch_bounds__(AB_THREADS, KB_GRID_MINB)
     kb_alpha_beta_grid(const bdesc *__restrict__ D, const bstate *__restrict__ S,
                        const int64_t *__restrict__ pre, int nprob) {
     const int64_t item = blockIdx.x;

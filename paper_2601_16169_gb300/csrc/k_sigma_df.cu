@@ -114,7 +114,12 @@ __global__ void __launch_bounds__(256) k_same_spin_df(ss_df_args a) {
 // Same work decomposition as k_alpha_beta (beta chunk x alpha row group,
 // slabs of C staged by cp.async, AB_EPT entries per thread); float-pair data.
 
-__global__ void __launch_bounds__(AB_THREADS, AB_MINB)
+// the float-pair operands need more registers than the FP64 kernel: 3 blocks
+// per SM keep them without spills
+#ifndef AB_DF_MINB
+#define AB_DF_MINB 3
+#endif
+__global__ void __launch_bounds__(AB_THREADS, AB_DF_MINB)
     k_alpha_beta_df(int64_t nb, int norb2, const int64_t *__restrict__ a_off,
                     const int32_t *__restrict__ a_src, const int32_t *__restrict__ a_tgt, const uint16_t *__restrict__ a_pq,
                     const int8_t *__restrict__ a_sgn, const int64_t *__restrict__ b_off,

@@ -65,20 +65,28 @@ struct ab_int {
         default: f(ab_int<(M)>{}); break;                                                      \
     }
 
-// 8 entries per thread fit in 80 registers, so 3 blocks (24 warps) share an
-// SM and hide the gather latency of V and the slabs; measured against 16
-// entries at 2 blocks per SM: 0.84 -> 0.90 of the FP64 peak at h2o29, 0.90 ->
-// 0.92 at scale36, 0.90 -> 0.93 at adjoint29 (12 entries at 2 blocks: 0.83).
+// 8 entries per thread in 64 registers and batches of 12 alpha singles (48 KB
+// of double-buffered slabs) let 4 blocks (32 warps) share an SM and hide the
+// gather latency of V and the slabs.  Measured fractions of the FP64 peak:
+//   16 entries, 2 blocks/SM, 16-single batches: 0.84 h2o29, 0.90 scale36;
+//    8 entries, 3 blocks/SM, 16-single batches: 0.89 h2o29, 0.92 adjoint29,
+//                                                 0.90 scale36;
+//    8 entries, 4 blocks/SM, 12-single batches: 0.91 h2o29, 0.93 adjoint29,
+//                                                 0.94 scale36;
+//    (4 blocks with 8-single batches: 0.91 scale36; 6 entries at 4 blocks:
+//    0.94 scale36, 0.945 adjoint29; 5 blocks spill.)
 #define AB_THREADS 256
 #ifndef AB_EPT
 #define AB_EPT 8                           // beta entries per thread
 #endif
 #ifndef AB_MINB
-#define AB_MINB 3                          // resident blocks per SM (launch bounds)
+#define AB_MINB 4                          // resident blocks per SM (launch bounds)
 #endif
 #define AB_ECAP (AB_THREADS * AB_EPT)      // beta entries per block
 #define AB_YW 256                          // beta rows (slab width) per block
-#define AB_NA 16                           // alpha singles staged per batch
+#ifndef AB_NA
+#define AB_NA 12                           // alpha singles staged per batch
+#endif
 static_assert(AB_EPT >= 1 && AB_EPT <= 16, "AB_DISPATCH covers 1..16 entry slots");
 #define AB_EPT_WIDE 16                     // entries per thread of the batched kernel
 #define AB_ECAP_WIDE (AB_THREADS * AB_EPT_WIDE)
