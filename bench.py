@@ -479,6 +479,46 @@ def solve_record(env, t, opts, workload):
             "roofline": sigma_roofline(prof, workload), "clocks": clocks}
 
 
+def e2e_sigma_pipelined(env, t, C, S, Cp, Sp, n):
+    """n sigma steps through the public API from pinned host buffers, wall
+    seconds.  Every step copies its input vector host -> device and its
+    sigma device -> host; the copies run on two copy streams and overlap the
+    neighbouring steps' sigma (two device buffer pairs, ordered by events),
+    as a pipeline of host-resident work would."""
+    torch, sqd, ctx = env.torch, env.sqd, env.ctx
+    main = env.stream
+    s_in, s_out = torch.cuda.Stream(env.dev), torch.cuda.Stream(env.dev)
+    bufs = [(C, S), (torch.empty_like(C), torch.empty_like(S))]
+    E = torch.cuda.Event
+    ev_in, ev_done, ev_out = [E(), E()], [E(), E()], [E(), E()]
+    env.sync()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(s_in):
+        bufs[0][0].copy_(Cp, non_blocking=True)
+        ev_in[0].record(s_in)
+    for k in range(n):
+        c, sg = bufs[k % 2]
+        main.wait_event(ev_in[k % 2])
+        if k >= 2:
+            main.wait_event(ev_out[k % 2])  # the copy-out of step k-2 left sg
+        sqd.sigma(ctx, t, c, sg)
+        ev_done[k % 2].record(main)
+        if k + 1 < n:
+            with torch.cuda.stream(s_in):
+                if k >= 1:
+                    s_in.wait_event(ev_done[(k + 1) % 2])  # step k-1 has read it
+                bufs[(k + 1) % 2][0].copy_(Cp, non_blocking=True)
+                ev_in[(k + 1) % 2].record(s_in)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ev_done[k % 2])
+            Sp.copy_(sg, non_blocking=True)
+            ev_out[k % 2].record(s_out)
+    env.sync()
+    dt = time.perf_counter() - t0
+    del bufs
+    return dt
+
+
 def headline(args, rank, world, local_rank):
     """The default line: sigma steps on the 4.0e8-determinant workload, e2e
     through host buffers, one converged solve, then the sub-records."""
@@ -503,7 +543,7 @@ def headline(args, rank, world, local_rank):
     fp64_dfma, fp64_dmma = ctx.measure_fp64_peaks()
 
     # e2e: the vector from pinned host memory, sigma back to it, per step
-    n_e2e = args.e2e_steps if args.e2e_steps is not None else max(1, min(args.steps, 3))
+    n_e2e = args.e2e_steps if args.e2e_steps is not None else max(1, min(args.steps, 5))
     e2e_s = 0.0
     if n_e2e:
         Cp = C_h.pin_memory()
@@ -512,13 +552,7 @@ def headline(args, rank, world, local_rank):
         env.sync()
         if world > 1:
             torch.distributed.barrier()
-        t0 = time.perf_counter()
-        for _ in range(n_e2e):
-            C.copy_(Cp, non_blocking=True)
-            sqd.sigma(ctx, t, C, S)
-            Sp.copy_(S, non_blocking=True)
-        env.sync()
-        e2e_s = time.perf_counter() - t0
+        e2e_s = e2e_sigma_pipelined(env, t, C, S, Cp, Sp, n_e2e)
         del Cp, Sp
     del C_h
 
@@ -552,7 +586,9 @@ def headline(args, rank, world, local_rank):
                                       "FP64 tensor MMAs (m8n8k4) at the SM clock in clocks"},
             "e2e": {"value": n_e2e * world / e2e_max if n_e2e else None, "unit": UNIT,
                     "steps": n_e2e, "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N,
-                    "path": "pinned host C -> device, sqd_sigma, device -> pinned host sigma"}
+                    "path": "pinned host C -> device, sqd_sigma, device -> pinned host sigma; "
+                            "the copies on two copy streams overlap the neighbouring steps' "
+                            "sigma (wall clock from the first copy-in to the last copy-out)"}
             if n_e2e else None,
             "clocks": clocks, "gpu_launches": launches,
         }
