@@ -67,7 +67,7 @@ SUBRECORDS = ("h2o29", "df", "batched", "adjoint", "stored")
 # (the nominal 1.25 TFLOP/s FP64 of GB300 at its maximum SM clock).
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 SIGMA_CLASSES = ("same_spin_alpha", "same_spin_beta", "alpha_beta")
-DAVIDSON_CLASSES = ("davidson", "ortho", "eigh")
+DAVIDSON_CLASSES = ("davidson", "ortho", "ortho_block", "gcols", "eigh")
 KERNEL_OF = {"same_spin_alpha": "k_same_spin", "same_spin_beta": "k_same_spin",
              "alpha_beta": "k_alpha_beta"}
 

@@ -327,7 +327,7 @@ int sqd_davidson(sqd_ctx *ctx, sqd_tables *tables, const sqd_options *opt,
  * determinant count): for each bucket, the kernel variant (16 entries per
  * thread over 4096-entry chunks in a persistent work-queue kernel, or 8
  * entries per thread over 2048-entry chunks in a grid) and the alpha-row
- * group count (0.5, 1 or 2 times the table's default split) are timed on
+ * group count (0.5, 1, 2 or 4 times the table's default split) are timed on
  * the first sigma of up to 4 of the bucket's largest subspaces.
  *
  * h_energies[nbatch] (host), d_C[b] (device, n_alpha*n_beta doubles each,
@@ -350,7 +350,7 @@ int sqd_batched_tuning(const sqd_ctx *ctx, double *group_scale, int *device_loop
 /* Fix the paired-singles tile of later sqd_davidson_batched calls on this
  * context instead of autotuning it (not in the paper; for tests and
  * measurements): entries_per_thread 16 (persistent kernel, wide chunks) or 8
- * (grid kernel, standard chunks) with group_scale 0.5, 1 or 2;
+ * (grid kernel, standard chunks) with group_scale 0.5, 1, 2 or 4;
  * entries_per_thread 0 restores autotuning.  Errors: SQD_EINVAL. */
 int sqd_batched_set_tile(sqd_ctx *ctx, int entries_per_thread, double group_scale);
 
@@ -399,12 +399,14 @@ int sqd_orbital_gradient(sqd_ctx *ctx, sqd_tables *tables, const double *d_rdm1,
  *   0 same_spin_alpha, 1 same_spin_beta, 2 alpha_beta, 3 transpose,
  *   4 tables, 5 strings, 6 davidson (Ritz vectors, residuals,
  *   preconditioner, restart), 7 rdm, 8 stored, 9 ortho (Davidson
- *   Gram-Schmidt and projected-matrix columns), 10 eigh (Rayleigh-Ritz
+ *   Gram-Schmidt of the new block against the basis), 10 eigh (Rayleigh-Ritz
  *   eigensolver), 11 batched (a whole sqd_davidson_batched call),
  *   12 batched_sigma, 13 batched_vector, 14 batched_eigh (the stages of the
  *   batched iteration loop: timed on the device with the global timer at the
  *   stage boundaries inside the captured loop, one region per iteration;
- *   flops and bytes summed over the subspaces each stage served).
+ *   flops and bytes summed over the subspaces each stage served),
+ *   15 gcols (Davidson: new columns of the projected matrix), 16 ortho_block
+ *   (Davidson: orthonormalisation within the new block).
  * sqd_profile_read returns, for one class, the class name (static string),
  * the number of regions, their summed event time in ms, and the
  * algorithmic FP64 flops and compulsory bytes booked for them (host

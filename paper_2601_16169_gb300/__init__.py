@@ -55,7 +55,7 @@ EXPORTED = [
 
 PROFILE_CLASSES = ["same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose", "tables",
                    "strings", "davidson", "rdm", "stored", "ortho", "eigh", "batched",
-                   "batched_sigma", "batched_vector", "batched_eigh"]
+                   "batched_sigma", "batched_vector", "batched_eigh", "gcols", "ortho_block"]
 
 
 class SQDError(RuntimeError):
@@ -462,7 +462,7 @@ def batched_tuning(ctx: Context, with_loop: bool = False):
 
 def batched_set_tile(ctx: Context, entries_per_thread: int = 0, group_scale: float = 1.0):
     """sqd_batched_set_tile: fix the paired-singles tile of later batched
-    solves (16 or 8 entries per thread, group scale 0.5 / 1 / 2); 0 restores
+    solves (16 or 8 entries per thread, group scale 0.5 / 1 / 2 / 4); 0 restores
     autotuning."""
     ctx._check(ctx._lib.sqd_batched_set_tile(ctx.handle, int(entries_per_thread),
                                              float(group_scale)))

@@ -149,7 +149,7 @@ static const char *k_prof_names[PROF_NCLASS] = {
     "same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose",
     "tables",          "strings",        "davidson",   "rdm", "stored",
     "ortho",           "eigh",           "batched",    "batched_sigma", "batched_vector",
-    "batched_eigh"};
+    "batched_eigh",    "gcols",          "ortho_block"};
 
 int sqd_profile_enable(sqd_ctx *ctx, int enable) {
     if (!ctx) return fail_noctx(SQD_EINVAL, "sqd_profile_enable: ctx is NULL");
@@ -677,11 +677,16 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
     // fused-pass sums: s1 = (V^T t, |r|^2, |t|^2), s2 = (V^T t', |t'|^2), s3 = restarted V^T t
     double *s1 = w.P + (int64_t)M * k, *s2 = s1 + (MDf + 2), *s3 = s2 + (MDf + 2);
 
-    // G[0..m, m0..m0+b) = V[0..m)^T W[m0..m0+b)
+    // G[0..m, m0..m0+b) = V[0..m)^T W[m0..m0+b) (one new vector of a one-root
+    // solve: the register-resident dot pass)
     auto g_cols = [&](int m, int m0, int b) -> int {
-        prof_begin(ctx, PROF_ORTHO);
-        SQD_TRY(launch_block_dot(ctx, w.Vb, N, m, w.Wb + (int64_t)m0 * N, N, b, N, w.partial, nbd,
-                                 w.G + (int64_t)m0 * M, M));
+        prof_begin(ctx, PROF_GCOLS);
+        if (b == 1 && MDf && m <= MDf)
+            SQD_TRY(launch_dots_one(ctx, MDf, w.Vb, N, m, w.Wb + (int64_t)m0 * N, N, w.partial,
+                                    nbr, w.G + (int64_t)m0 * M));
+        else
+            SQD_TRY(launch_block_dot(ctx, w.Vb, N, m, w.Wb + (int64_t)m0 * N, N, b, N, w.partial,
+                                     nbd, w.G + (int64_t)m0 * M, M));
         prof_end(ctx, 2.0 * m * b * dN, 8.0 * (m + b) * dN);
         return SQD_OK;
     };
@@ -697,7 +702,7 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
             if (acc != j)
                 SQD_CUDA(ctx, cudaMemcpyAsync(dst, T + (int64_t)j * N, sizeof(double) * N,
                                               cudaMemcpyDeviceToDevice, st));
-            prof_begin(ctx, PROF_ORTHO);
+            prof_begin(ctx, PROF_ORTHO_BLOCK);
             for (int pass = 0; pass < 2 && acc > 0; pass++) {
                 SQD_TRY(launch_multidot(ctx, T, N, acc, dst, N, w.partial, nblk, w.dots));
                 SQD_TRY(launch_gemv_sub(ctx, T, N, acc, w.dots, dst, N));
@@ -741,7 +746,7 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
         hG.assign((size_t)b * b, 0.0);
         hZ.assign((size_t)b * b, 0.0);
         for (int round = 0; round < 2; round++) {
-            prof_begin(ctx, PROF_ORTHO);
+            prof_begin(ctx, PROF_ORTHO_BLOCK);
             SQD_TRY(launch_block_dot(ctx, T, N, b, T, N, b, N, w.partial, nbd, w.P, b));
             prof_end(ctx, 2.0 * b * b * dN, 16.0 * b * dN);
             SQD_CUDA(ctx, cudaMemcpyAsync(hG.data(), w.P, sizeof(double) * b * b,
@@ -780,7 +785,7 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
             }
             SQD_CUDA(ctx, cudaMemcpyAsync(Zd, hZ.data(), sizeof(double) * b * b,
                                           cudaMemcpyHostToDevice, st));
-            prof_begin(ctx, PROF_ORTHO);
+            prof_begin(ctx, PROF_ORTHO_BLOCK);
             SQD_TRY(launch_combine(ctx, T, N, b, Zd, b, b, w.Tmp, N, N));
             SQD_CUDA(ctx, cudaMemcpyAsync(T, w.Tmp, sizeof(double) * b * N,
                                           cudaMemcpyDeviceToDevice, st));
@@ -1226,9 +1231,9 @@ int sqd_batched_set_tile(sqd_ctx *ctx, int entries_per_thread, double group_scal
         return SQD_OK;
     }
     if ((entries_per_thread != 8 && entries_per_thread != 16) ||
-        (group_scale != 0.5 && group_scale != 1.0 && group_scale != 2.0))
+        (group_scale != 0.5 && group_scale != 1.0 && group_scale != 2.0 && group_scale != 4.0))
         return sqd_fail(ctx, SQD_EINVAL,
-                        "tile must be 8 or 16 entries per thread with scale 0.5, 1 or 2");
+                        "tile must be 8 or 16 entries per thread with scale 0.5, 1, 2 or 4");
     ctx->batched_force_ept = entries_per_thread;
     ctx->batched_force_scale = group_scale;
     return SQD_OK;

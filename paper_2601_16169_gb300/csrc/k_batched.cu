@@ -546,6 +546,38 @@ __global__ void __launch_bounds__(BV_THREADS) kb_gs_update2(const bdesc *__restr
     BM_DISPATCH(st.m, go);
 }
 
+template <int MB>
+__device__ __forceinline__ void gcol_body(const bdesc &d, const slice_t &sl, double *red) {
+    const double *__restrict__ x = d.W + (int64_t)(MB - 1) * d.N;
+    double acc[MB];
+#pragma unroll
+    for (int i = 0; i < MB; i++) acc[i] = 0.0;
+    for (int64_t n = sl.lo + threadIdx.x; n < sl.hi; n += BV_THREADS) {
+        double vv[MB];
+#pragma unroll
+        for (int i = 0; i < MB; i++) vv[i] = d.V[(int64_t)i * d.N + n];
+        const double xn = x[n];
+#pragma unroll
+        for (int i = 0; i < MB; i++) acc[i] = fma(vv[i], xn, acc[i]);
+    }
+    const double ex[1] = {0.0};
+    store_sums<MB, 1>(d, sl.s, acc, ex, red);  // rows 0..m-1 (row m unused)
+}
+
+// new column of G: partials of V[i] . W[m-1], i < m (after m was incremented),
+// every basis value of an element loaded once
+__global__ void __launch_bounds__(BV_THREADS) kb_gcol(const bdesc *__restrict__ D,
+                                                      const bstate *__restrict__ S,
+                                                      const int64_t *__restrict__ pre, int nprob) {
+    __shared__ double red[(BV_THREADS / 32) * (BM + 1)];
+    const slice_t sl = slice_of(D, pre, nprob, blockIdx.x);
+    const bstate &st = S[sl.b];
+    if (!st.newvec) return;
+    const bdesc &d = D[sl.b];
+    auto go = [&](auto mb) { gcol_body<decltype(mb)::value>(d, sl, red); };
+    BM_DISPATCH(st.m, go);
+}
+
 // partial dot products on a slice.  mode 1: V[m] . V[m] (the explicit norm,
 // subspaces with expl set); mode 2: V[i] . W[m-1], i < m (new column of G,
 // after m was incremented)
@@ -874,8 +906,12 @@ static int launch_sigma_stages(sqd_ctx *ctx, batched_plan &p) {
 }
 
 static int launch_gram(sqd_ctx *ctx, batched_plan &p, int mode) {
-    kb_gram<<<(unsigned)p.tot_vec, BV_THREADS, 0, ctx->stream>>>(p.D, p.S, p.pre_vec, p.nprob,
-                                                                 mode);
+    if (mode == 2)
+        kb_gcol<<<(unsigned)p.tot_vec, BV_THREADS, 0, ctx->stream>>>(p.D, p.S, p.pre_vec,
+                                                                     p.nprob);
+    else
+        kb_gram<<<(unsigned)p.tot_vec, BV_THREADS, 0, ctx->stream>>>(p.D, p.S, p.pre_vec, p.nprob,
+                                                                     mode);
     SQD_LAUNCHED(ctx);
     kb_gram_final<<<p.nprob, 128, 0, ctx->stream>>>(p.D, p.S, mode, p.M);
     SQD_LAUNCHED(ctx);
@@ -935,8 +971,8 @@ static int launch_iteration(sqd_ctx *ctx, batched_plan &p, const bparams &P) {
 // thread, 2 blocks per SM; 1: grid, standard chunks, AB_EPT per thread,
 // AB_MINB blocks per SM) and the alpha-row group count (the table's default
 // split times a scale).  Group arrays are built once per candidate scale.
-static const double kAbScales[] = {0.5, 1.0, 2.0};
-#define AB_NSCALE 3
+static const double kAbScales[] = {0.5, 1.0, 2.0, 4.0};
+#define AB_NSCALE 4
 
 struct ab_choice {
     std::vector<int64_t *> groups;  // per scale: device group rows

@@ -967,6 +967,32 @@ struct mb_int {
         default: f(mb_int<16>{}); break;                                                      \
     }
 
+// V_i . x for i < MB (the new column of the projected matrix of a one-root
+// solve, x = W_new): every load of an element's MB basis values in flight at
+// once, per-block sums in one barrier.  A block-dot tile of m x 1 outputs
+// leaves most threads idle; this pass keeps the FP64 pipe fed instead.
+template <int MB>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_dots_one(const double *__restrict__ V, int64_t ld, const double *__restrict__ x,
+               int64_t n, double *__restrict__ partial) {
+    __shared__ double red[(RED_THREADS / 32) * MB];
+    double acc[MB];
+#pragma unroll
+    for (int i = 0; i < MB; i++) acc[i] = 0.0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double vv[MB];
+#pragma unroll
+        for (int i = 0; i < MB; i++) vv[i] = V[(int64_t)i * ld + p];
+        const double xp = x[p];
+#pragma unroll
+        for (int i = 0; i < MB; i++) acc[i] = fma(vv[i], xp, acc[i]);
+    }
+    int i;
+    double v;
+    if (block_sums<MB>(acc, red, &i, &v)) partial[(int64_t)blockIdx.x * MB + i] = v;
+}
+
 // out[i] = sum over blocks b of partial[b * stride + i], i < cnt (fixed order)
 __global__ void k_sum_partials(const double *__restrict__ partial, int nblk, int stride,
                                int cnt, double *__restrict__ out) {
@@ -1060,6 +1086,23 @@ int launch_gs_update_scale(sqd_ctx *ctx, int MD, const double *V, int64_t ld, in
         k_gs_update_scale<MB><<<nblk, RED_THREADS, 0, st>>>(V, ld, P, scale, T, n);
     };
     MB_DISPATCH(m, go);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// out[i] = V_i . x for i < m <= MD (contiguous outputs); partial: nblk * m
+int launch_dots_one(sqd_ctx *ctx, int MD, const double *V, int64_t ld, int m, const double *x,
+                    int64_t n, double *partial, int nblk, double *out) {
+    if (m < 1 || m > MD || MD != 16)
+        return sqd_fail(ctx, SQD_EINVAL, "one-vector dots: m = %d out of range", m);
+    cudaStream_t st = ctx->stream;
+    auto go = [&](auto mb) {
+        constexpr int MB = decltype(mb)::value;
+        k_dots_one<MB><<<nblk, RED_THREADS, 0, st>>>(V, ld, x, n, partial);
+    };
+    MB_DISPATCH(m, go);
+    SQD_LAUNCHED(ctx);
+    k_sum_partials<<<1, 64, 0, st>>>(partial, nblk, m, m, out);
     SQD_LAUNCHED(ctx);
     return SQD_OK;
 }

@@ -25,12 +25,14 @@ enum prof_class {
     PROF_DAVIDSON,        // Davidson Ritz vectors, residuals, preconditioner, restart
     PROF_RDM,             // density matrices
     PROF_STORED,          // stored-H sparse matrix-vector product
-    PROF_ORTHO,           // Davidson Gram-Schmidt and projected-matrix columns
+    PROF_ORTHO,           // Davidson Gram-Schmidt of the new block against the basis
     PROF_EIGH,            // Davidson Rayleigh-Ritz eigensolver
     PROF_BATCHED,         // a whole batched solve (setup, tuning, loop, outputs)
     PROF_B_SIGMA,         // batched loop: sigma stages (device-timed per iteration)
     PROF_B_VECTOR,        // batched loop: Ritz, restart, correction, Gram-Schmidt, G columns
     PROF_B_EIGH,          // batched loop: the per-subspace Jacobi eigensolves
+    PROF_GCOLS,           // Davidson: new columns of the projected matrix G = V^T W
+    PROF_ORTHO_BLOCK,     // Davidson: orthonormalisation within the new block
     PROF_NCLASS
 };
 
@@ -278,6 +280,8 @@ int launch_gs_update_scale(sqd_ctx *, int MD, const double *V, int64_t ld, int m
                            const double *P, double scale, double *T, int64_t n, int nblk);
 int launch_combine_inplace(sqd_ctx *, double *A, int64_t lda, int m, const double *Z, int ldz,
                            int r, int64_t n);
+int launch_dots_one(sqd_ctx *, int MD, const double *V, int64_t ld, int m, const double *x,
+                    int64_t n, double *partial, int nblk, double *out);
 int launch_project_coeffs(sqd_ctx *, const double *Z, int ldz, int m, int r, const double *Pold,
                           double *Pnew);
 
