@@ -170,10 +170,14 @@ int launch_combine_sub(sqd_ctx *ctx, const double *A, int64_t lda, int m, const 
 // product split over n.  Each block walks its n-range in tiles of kc columns
 // staged in shared memory (every element of A and X is read from HBM once),
 // kc chosen so that the m + b rows of a tile fill about BD_TILE doubles.  The
-// m*b outputs are spread over the 256 threads; when there are fewer outputs
-// than threads, g = 256 / (m*b) threads share an output and split the tile's
-// columns, and their sums are added at the end.  The per-block partials are
-// summed in a fixed order, so results do not depend on timing.
+// work of a tile is m*b outputs of kc multiply-adds; it is cut into m*b*g
+// units (an output and every g-th column of the tile), g chosen on the host
+// so that the units spread evenly over the 256 threads: with m*b = 320, for
+// instance, one output per thread would leave 64 threads with a second one
+// and the rest idle for half the tile, where g = 4 gives every thread 5
+// units of kc/4 columns.  The g partial sums of an output are added in a
+// fixed order at the end, and the per-block partials are summed in a fixed
+// order too, so results do not depend on timing.
 #define BD_TILE 4608
 #define BD_MAXB 32
 #define BD_OUT 16
@@ -191,17 +195,35 @@ static int block_dot_kc(int m, int b) {
     return kc < 32 ? 32 : (kc > 512 ? 512 : kc);
 }
 
+// column split g (a power of two dividing kc, at most BD_OUT units per
+// thread) with the shortest per-thread path ceil(mb g / 256) * kc / g; ties
+// go to the smaller g
+static int block_dot_split(int mb, int kc) {
+    int best_g = 1;
+    long best = -1;
+    for (int g = 1; g <= RED_THREADS && g <= kc; g *= 2) {
+        if ((long)mb * g > (long)RED_THREADS * BD_OUT) break;
+        if (kc % g) continue;
+        const long upt = ((long)mb * g + RED_THREADS - 1) / RED_THREADS;
+        const long cost = upt * (kc / g);
+        if (best < 0 || cost < best) {
+            best = cost;
+            best_g = g;
+        }
+    }
+    return best_g;
+}
+
 __global__ void __launch_bounds__(RED_THREADS)
     k_block_dot_partial(const double *__restrict__ A, int64_t lda, int m,
                         const double *__restrict__ X, int64_t ldx, int b, int64_t n, int kc,
-                        double *__restrict__ partial, const int *__restrict__ gate) {
+                        int g, double *__restrict__ partial, const int *__restrict__ gate) {
     if (gate && *gate == 0) return;  // a pass the device decided to skip
     extern __shared__ double bd_sh[];
     const int ld = kc + 1;
     double *As = bd_sh, *Xs = bd_sh + (size_t)m * ld;
     const int mb = m * b;
-    const int g = (mb >= RED_THREADS) ? 1 : RED_THREADS / mb;  // threads per output
-    const int tg = threadIdx.x / mb;                             // column group (g > 1)
+    const int U = mb * g;  // units: (output, column group)
     const int64_t per = (n + gridDim.x - 1) / gridDim.x;
     const int64_t lo = per * blockIdx.x, hi = min(n, lo + per);
     double acc[BD_OUT];
@@ -217,43 +239,32 @@ __global__ void __launch_bounds__(RED_THREADS)
             bd_sh[(size_t)r * ld + kk] = (kk < len) ? src[c0 + kk] : 0.0;
         }
         __syncthreads();
-        if (g == 1) {
 #pragma unroll
-            for (int q = 0; q < BD_OUT; q++) {
-                const int o = threadIdx.x + q * RED_THREADS;
-                if (o < mb) {
-                    const double *ar = As + (size_t)(o % m) * ld, *xr = Xs + (size_t)(o / m) * ld;
-                    double s = acc[q];
-#pragma unroll 8
-                    for (int kk = 0; kk < kc; kk++) s = fma(ar[kk], xr[kk], s);
-                    acc[q] = s;
-                }
-            }
-        } else if (tg < g) {
-            const int o = threadIdx.x - tg * mb;
-            const double *ar = As + (size_t)(o % m) * ld, *xr = Xs + (size_t)(o / m) * ld;
-            double s = acc[0];
+        for (int q = 0; q < BD_OUT; q++) {
+            const int u = threadIdx.x + q * RED_THREADS;
+            if (u < U) {
+                const int o = u / g, tg = u - o * g;
+                const double *ar = As + (size_t)(o % m) * ld, *xr = Xs + (size_t)(o / m) * ld;
+                double s = acc[q];
 #pragma unroll 4
-            for (int kk = tg; kk < kc; kk += g) s = fma(ar[kk], xr[kk], s);
-            acc[0] = s;
+                for (int kk = tg; kk < kc; kk += g) s = fma(ar[kk], xr[kk], s);
+                acc[q] = s;
+            }
         }
         __syncthreads();
     }
-    if (g == 1) {
+    // unit sums to shared memory (U <= 4096 doubles: the launch sizes the
+    // dynamic shared memory for it), then each output adds its g units in order
 #pragma unroll
-        for (int q = 0; q < BD_OUT; q++) {
-            const int o = threadIdx.x + q * RED_THREADS;
-            if (o < mb) partial[(int64_t)blockIdx.x * mb + o] = acc[q];
-        }
-    } else {
-        // fixed-order sum over the g column groups of each output
-        bd_sh[threadIdx.x] = (tg < g) ? acc[0] : 0.0;
-        __syncthreads();
-        if (threadIdx.x < mb) {
-            double s = 0.0;
-            for (int q = 0; q < g; q++) s += bd_sh[threadIdx.x + q * mb];
-            partial[(int64_t)blockIdx.x * mb + threadIdx.x] = s;
-        }
+    for (int q = 0; q < BD_OUT; q++) {
+        const int u = threadIdx.x + q * RED_THREADS;
+        if (u < U) bd_sh[u] = acc[q];
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < mb; o += RED_THREADS) {
+        double s = 0.0;
+        for (int q = 0; q < g; q++) s += bd_sh[o * g + q];
+        partial[(int64_t)blockIdx.x * mb + o] = s;
     }
 }
 
@@ -275,10 +286,13 @@ int launch_block_dot(sqd_ctx *ctx, const double *A, int64_t lda, int m, const do
     if (m > JAC_MAX || b > BD_MAXB || m * b > RED_THREADS * BD_OUT)
         return sqd_fail(ctx, SQD_EINVAL, "block dot of %d x %d vectors out of range", m, b);
     const int kc = block_dot_kc(m, b);
+    const int g = block_dot_split(m * b, kc);
     size_t shm = sizeof(double) * (size_t)(m + b) * (kc + 1);
-    if (shm < sizeof(double) * RED_THREADS) shm = sizeof(double) * RED_THREADS;
-    // at most (112 + 32) rows x 33 columns = 38 KB: within the default 48 KB
-    k_block_dot_partial<<<nblk, RED_THREADS, shm, ctx->stream>>>(A, lda, m, X, ldx, b, n, kc,
+    const size_t shu = sizeof(double) * (size_t)m * b * g;  // the unit sums
+    if (shm < shu) shm = shu;
+    // tiles fill about BD_TILE + (m + b) doubles, unit sums at most
+    // RED_THREADS * BD_OUT doubles: 37 KB and 32 KB, within the default 48 KB
+    k_block_dot_partial<<<nblk, RED_THREADS, shm, ctx->stream>>>(A, lda, m, X, ldx, b, n, kc, g,
                                                                   partial, gate);
     SQD_LAUNCHED(ctx);
     k_block_dot_final<<<(m * b + 127) / 128, 128, 0, ctx->stream>>>(partial, nblk, m, b, out, ldo,
