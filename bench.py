@@ -178,13 +178,25 @@ def _cores():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
+_VECTORS = {}
+
+
+def _input_vector(N):
+    """The seeded input vector of N determinants (drawn once per size: at
+    4e8 determinants it is 3.2 GB of normal draws)."""
+    if N not in _VECTORS:
+        _VECTORS.clear()
+        _VECTORS[N] = si.random_vectors(1, N, 13)[0]
+    return _VECTORS[N]
+
+
 def oracle_sigma_rate(w, rows_n, seed=0):
     """The oracle's sigma (as it stands) on rows_n seeded rows of one sigma
     of workload w on the host cores: (rows per second, seconds, rows)."""
     import oracle
     oracle.lib()
     N = w.ndet
-    C = si.random_vectors(1, N, 13)[0]
+    C = _input_vector(N)
     rows = np.sort(np.random.default_rng(seed).choice(N, size=min(rows_n, N), replace=False))
     t0 = time.perf_counter()
     oracle.sigma(w.norb, w.h, w.V, 0.0, w.strings_a, w.strings_b, C, rows=rows)
@@ -543,7 +555,7 @@ def headline(args, rank, world, local_rank):
     fp64_dfma, fp64_dmma = ctx.measure_fp64_peaks()
 
     # e2e: the vector from pinned host memory, sigma back to it, per step
-    n_e2e = args.e2e_steps if args.e2e_steps is not None else max(1, min(args.steps, 5))
+    n_e2e = args.e2e_steps if args.e2e_steps is not None else max(1, min(args.steps, 10))
     e2e_s = 0.0
     if n_e2e:
         Cp = C_h.pin_memory()
