@@ -887,7 +887,8 @@ def run_batched(args, rank, world, local_rank, with_cpu=True):
            "loop_in_one_graph": device_loop,
            "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items() if v["ms"]},
            "classes": class_record(prof, [k for k in ("batched", "batched_sigma",
-                                                      "batched_vector", "batched_eigh")
+                                                      "batched_sigma_ab", "batched_vector",
+                                                      "batched_eigh")
                                           if k in prof]),
            "roofline": batched_roofline(prof),
            "clocks": clocks, "gpu_launches": launches}

@@ -406,7 +406,8 @@ int sqd_orbital_gradient(sqd_ctx *ctx, sqd_tables *tables, const double *d_rdm1,
  *   stage boundaries inside the captured loop, one region per iteration;
  *   flops and bytes summed over the subspaces each stage served),
  *   15 gcols (Davidson: new columns of the projected matrix), 16 ortho_block
- *   (Davidson: orthonormalisation within the new block).
+ *   (Davidson: orthonormalisation within the new block), 17 batched_sigma_ab
+ *   (the paired-singles part of batched_sigma, timed the same way).
  * sqd_profile_read returns, for one class, the class name (static string),
  * the number of regions, their summed event time in ms, and the
  * algorithmic FP64 flops and compulsory bytes booked for them (host

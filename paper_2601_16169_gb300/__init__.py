@@ -55,7 +55,8 @@ EXPORTED = [
 
 PROFILE_CLASSES = ["same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose", "tables",
                    "strings", "davidson", "rdm", "stored", "ortho", "eigh", "batched",
-                   "batched_sigma", "batched_vector", "batched_eigh", "gcols", "ortho_block"]
+                   "batched_sigma", "batched_vector", "batched_eigh", "gcols", "ortho_block",
+                   "batched_sigma_ab"]
 
 
 class SQDError(RuntimeError):

@@ -149,7 +149,7 @@ static const char *k_prof_names[PROF_NCLASS] = {
     "same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose",
     "tables",          "strings",        "davidson",   "rdm", "stored",
     "ortho",           "eigh",           "batched",    "batched_sigma", "batched_vector",
-    "batched_eigh",    "gcols",          "ortho_block"};
+    "batched_eigh",    "gcols",          "ortho_block", "batched_sigma_ab"};
 
 int sqd_profile_enable(sqd_ctx *ctx, int enable) {
     if (!ctx) return fail_noctx(SQD_EINVAL, "sqd_profile_enable: ctx is NULL");

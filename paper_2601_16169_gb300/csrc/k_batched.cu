@@ -40,7 +40,8 @@
 
 struct bdesc {
     int64_t na, nb, N, nsl;
-    double sflops;  // algorithmic FP64 flops of one sigma (profiling)
+    double sflops;   // algorithmic FP64 flops of one sigma (profiling)
+    double abflops;  // the same for its paired-singles term
     ss_args ssa;  // alpha side (C, S filled from the state)
     ss_args ssb;  // beta side on T -> U
     ab_args ab;   // paired singles over the wide chunks (persistent kernel)
@@ -703,14 +704,16 @@ __global__ void kb_loop_control(const int *__restrict__ active, int *__restrict_
 
 // Stage timer of the batched loop (profiling only; one warp).  Stamped at
 // the stage boundaries inside the captured loop: the global-timer interval
-// since the previous stamp is booked to `stage` (0 sigma, 1 vector work,
-// 2 eigensolve; -1 only sets the start), with the algorithmic work of the
-// subspaces the stage served: sigma flops of those given a new vector;
+// since the previous stamp is booked to `stage` (0 sigma apart from its
+// paired singles, 1 vector work, 2 eigensolve, 3 the paired singles; -1 only
+// sets the start), with the algorithmic work of the subspaces the stage
+// served: sigma flops of those given a new vector (booked by the stamp that
+// ends the sigma stage, part 0; part 1 books time only), paired-singles flops;
 // vector bytes and flops of the one-vector Davidson step (Ritz pair, residual,
 // correction, two Gram-Schmidt passes, normalisation in three fused passes:
 // 4 m + 6 vector passes and 12 m + 12 flops per element; part 1) or of the
 // new G column (m + 1 passes, 2 m flops; part 2).
-// acc: [0..3) ns, [3..6) flops, [6..9) bytes, [9..12) regions, [12] last stamp
+// acc: [0..4) ns, [4..8) flops, [8..12) bytes, [12..16) regions, [16] last stamp
 __global__ void kb_stamp(const bdesc *__restrict__ D, const bstate *__restrict__ S, int nprob,
                          int stage, int part, double *__restrict__ acc) {
     unsigned long long now;
@@ -721,8 +724,10 @@ __global__ void kb_stamp(const bdesc *__restrict__ D, const bstate *__restrict__
             if (!S[b].newvec) continue;
             const double N = (double)D[b].N;
             const int m = S[b].m;  // after the new vector was appended
-            if (stage == 0) {
+            if (stage == 0 && part == 0) {
                 f += D[b].sflops;
+            } else if (stage == 3) {
+                f += D[b].abflops;
             } else if (stage == 1 && part == 1) {
                 by += 8.0 * N * (4.0 * (m - 1) + 6.0);
                 f += N * (12.0 * (m - 1) + 12.0);
@@ -738,12 +743,14 @@ __global__ void kb_stamp(const bdesc *__restrict__ D, const bstate *__restrict__
         }
     }
     if (threadIdx.x == 0) {
-        unsigned long long *last = reinterpret_cast<unsigned long long *>(acc + 12);
+        unsigned long long *last = reinterpret_cast<unsigned long long *>(acc + 16);
         if (stage >= 0) {
             acc[stage] += (double)(now - *last);
-            acc[3 + stage] += f;
-            acc[6 + stage] += by;
-            if (stage != 1 || part == 1) acc[9 + stage] += 1.0;
+            acc[4 + stage] += f;
+            acc[8 + stage] += by;
+            if ((stage == 0 && part == 0) || (stage == 1 && part == 1) || stage == 2 ||
+                stage == 3)
+                acc[12 + stage] += 1.0;
         }
         *last = now;
     }
@@ -806,7 +813,7 @@ __global__ void __launch_bounds__(256) kb_guess(const bdesc *__restrict__ D,
 
 struct batched_plan {
     int nprob = 0, M = 0;
-    double *stamps = nullptr;  // stage timer accumulators (profiling), 13 doubles
+    double *stamps = nullptr;  // stage timer accumulators (profiling), 17 doubles
     std::vector<bdesc> hdesc;
     bdesc *D = nullptr;
     bstate *S = nullptr;
@@ -885,7 +892,10 @@ static int launch_ab_stage(sqd_ctx *ctx, batched_plan &p) {
 
 // launch the three sigma stages for every subspace flagged newvec (kernels
 // only, so the sequence can be the body of a conditional graph node)
-static int launch_sigma_stages(sqd_ctx *ctx, batched_plan &p) {
+static int stamp(sqd_ctx *ctx, batched_plan &p, int stage, int part = 0);
+
+// in_loop: inside the captured iteration, where the stage timer runs
+static int launch_sigma_stages(sqd_ctx *ctx, batched_plan &p, bool in_loop = false) {
     const int n = p.nprob;
     const int sm = ctx->sm_count;
     kb_zero_counters<<<1, 32, 0, ctx->stream>>>(p.counters, 5);
@@ -895,7 +905,9 @@ static int launch_sigma_stages(sqd_ctx *ctx, batched_plan &p) {
     kb_transpose<0><<<8 * sm, dim3(32, 8), 0, ctx->stream>>>(p.D, p.S, p.pre_t0, n,
                                                              p.counters + 1);
     SQD_LAUNCHED(ctx);
+    if (in_loop) SQD_TRY(stamp(ctx, p, 0, 1));
     SQD_TRY(launch_ab_stage(ctx, p));
+    if (in_loop) SQD_TRY(stamp(ctx, p, 3));
     kb_same_spin<false><<<8 * sm, 256, 0, ctx->stream>>>(p.D, p.S, p.pre_ssb, n,
                                                          p.counters + 3);
     SQD_LAUNCHED(ctx);
@@ -918,7 +930,7 @@ static int launch_gram(sqd_ctx *ctx, batched_plan &p, int mode) {
     return SQD_OK;
 }
 
-static int stamp(sqd_ctx *ctx, batched_plan &p, int stage, int part = 0) {
+static int stamp(sqd_ctx *ctx, batched_plan &p, int stage, int part) {
     if (!p.stamps) return SQD_OK;
     kb_stamp<<<1, 32, 0, ctx->stream>>>(p.D, p.S, p.nprob, stage, part, p.stamps);
     SQD_LAUNCHED(ctx);
@@ -957,7 +969,7 @@ static int launch_iteration(sqd_ctx *ctx, batched_plan &p, const bparams &P) {
     kb_scale_new<<<vb, BV_THREADS, 0, ctx->stream>>>(p.D, p.S, p.pre_vec, n);
     SQD_LAUNCHED(ctx);
     SQD_TRY(stamp(ctx, p, 1, 1));
-    SQD_TRY(launch_sigma_stages(ctx, p));
+    SQD_TRY(launch_sigma_stages(ctx, p, true));
     SQD_TRY(stamp(ctx, p, 0));
     SQD_TRY(launch_gram(ctx, p, 2));
     kb_count_active<<<1, 256, 0, ctx->stream>>>(p.S, n, p.d_active);
@@ -1093,6 +1105,7 @@ int davidson_batched_impl(sqd_ctx *ctx, int nprob, sqd_tables *const *tables,
             double fa, fb, fab;
             sigma_work(t, &fa, &fb, &fab);
             d.sflops = fa + fb + fab;
+            d.abflops = fab;
         }
         // persistent kernel: wide chunks; grid kernel: the standard ones
         d.abn = d.ab;
@@ -1115,9 +1128,9 @@ int davidson_batched_impl(sqd_ctx *ctx, int nprob, sqd_tables *const *tables,
         return fail(rc);
     if ((rc = plan_alloc(ctx, p, (void **)&p.d_active, sizeof(int))) != SQD_OK) return fail(rc);
     if (ctx->prof) {
-        if ((rc = plan_alloc(ctx, p, (void **)&p.stamps, sizeof(double) * 13)) != SQD_OK)
+        if ((rc = plan_alloc(ctx, p, (void **)&p.stamps, sizeof(double) * 17)) != SQD_OK)
             return fail(rc);
-        if (cudaMemsetAsync(p.stamps, 0, sizeof(double) * 13, ctx->stream) != cudaSuccess)
+        if (cudaMemsetAsync(p.stamps, 0, sizeof(double) * 17, ctx->stream) != cudaSuccess)
             return fail(sqd_fail(ctx, SQD_ECUDA, "memset failed"));
     }
     if ((rc = upload_prefix(ctx, p, pssa, &p.pre_ssa)) != SQD_OK) return fail(rc);
@@ -1342,16 +1355,18 @@ int davidson_batched_impl(sqd_ctx *ctx, int nprob, sqd_tables *const *tables,
     cudaStreamDestroy(cap);
     prof_end(ctx, 0.0, 0.0);
     if (p.stamps) {
-        double acc[13];
+        double acc[17];
         if (cudaMemcpyAsync(acc, p.stamps, sizeof(acc), cudaMemcpyDeviceToHost, ctx->stream) ==
                 cudaSuccess &&
             cudaStreamSynchronize(ctx->stream) == cudaSuccess) {
-            const int cls[3] = {PROF_B_SIGMA, PROF_B_VECTOR, PROF_B_EIGH};
-            for (int q = 0; q < 3; q++) {
+            // the sigma class holds the whole stage, its paired singles included
+            acc[0] += acc[3];
+            const int cls[4] = {PROF_B_SIGMA, PROF_B_VECTOR, PROF_B_EIGH, PROF_B_SIGMA_AB};
+            for (int q = 0; q < 4; q++) {
                 ctx->cls_ms[cls[q]] += acc[q] * 1e-6;
-                ctx->cls_flops[cls[q]] += acc[3 + q];
-                ctx->cls_bytes[cls[q]] += acc[6 + q];
-                ctx->cls_launches[cls[q]] += (int64_t)acc[9 + q];
+                ctx->cls_flops[cls[q]] += acc[4 + q];
+                ctx->cls_bytes[cls[q]] += acc[8 + q];
+                ctx->cls_launches[cls[q]] += (int64_t)acc[12 + q];
             }
         }
     }

@@ -33,6 +33,7 @@ enum prof_class {
     PROF_B_EIGH,          // batched loop: the per-subspace Jacobi eigensolves
     PROF_GCOLS,           // Davidson: new columns of the projected matrix G = V^T W
     PROF_ORTHO_BLOCK,     // Davidson: orthonormalisation within the new block
+    PROF_B_SIGMA_AB,      // batched loop: the paired-singles part of the sigma stage
     PROF_NCLASS
 };
 
