@@ -786,10 +786,14 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
             SQD_CUDA(ctx, cudaMemcpyAsync(Zd, hZ.data(), sizeof(double) * b * b,
                                           cudaMemcpyHostToDevice, st));
             prof_begin(ctx, PROF_ORTHO_BLOCK);
-            SQD_TRY(launch_combine(ctx, T, N, b, Zd, b, b, w.Tmp, N, N));
-            SQD_CUDA(ctx, cudaMemcpyAsync(T, w.Tmp, sizeof(double) * b * N,
-                                          cudaMemcpyDeviceToDevice, st));
-            prof_end(ctx, 1.0 * b * (b + 1) * dN, 8.0 * 4.0 * b * dN);
+            if (b <= 8) {
+                SQD_TRY(launch_combine_inplace(ctx, T, N, b, Zd, b, b, N));
+            } else {
+                SQD_TRY(launch_combine(ctx, T, N, b, Zd, b, b, w.Tmp, N, N));
+                SQD_CUDA(ctx, cudaMemcpyAsync(T, w.Tmp, sizeof(double) * b * N,
+                                              cudaMemcpyDeviceToDevice, st));
+            }
+            prof_end(ctx, 1.0 * b * (b + 1) * dN, 8.0 * 2.0 * b * dN);
         }
         *nacc = b;
         *ok = true;
@@ -1073,12 +1077,17 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
                 int r = 0;
                 SQD_TRY(restart_basis(&r));
                 prof_begin(ctx, PROF_DAVIDSON);
-                SQD_TRY(launch_combine(ctx, w.Vb, N, m, w.Z, M, r, w.Tmp, N, N));
-                SQD_CUDA(ctx, cudaMemcpyAsync(w.Vb, w.Tmp, sizeof(double) * r * N,
-                                              cudaMemcpyDeviceToDevice, st));
-                SQD_TRY(launch_combine(ctx, w.Wb, N, m, w.Z, M, r, w.Tmp, N, N));
-                SQD_CUDA(ctx, cudaMemcpyAsync(w.Wb, w.Tmp, sizeof(double) * r * N,
-                                              cudaMemcpyDeviceToDevice, st));
+                if (r <= 8) {  // one pass, in place
+                    SQD_TRY(launch_combine_inplace(ctx, w.Vb, N, m, w.Z, M, r, N));
+                    SQD_TRY(launch_combine_inplace(ctx, w.Wb, N, m, w.Z, M, r, N));
+                } else {
+                    SQD_TRY(launch_combine(ctx, w.Vb, N, m, w.Z, M, r, w.Tmp, N, N));
+                    SQD_CUDA(ctx, cudaMemcpyAsync(w.Vb, w.Tmp, sizeof(double) * r * N,
+                                                  cudaMemcpyDeviceToDevice, st));
+                    SQD_TRY(launch_combine(ctx, w.Wb, N, m, w.Z, M, r, w.Tmp, N, N));
+                    SQD_CUDA(ctx, cudaMemcpyAsync(w.Wb, w.Tmp, sizeof(double) * r * N,
+                                                  cudaMemcpyDeviceToDevice, st));
+                }
                 // projected matrix of the new basis: G' = Z^T G Z
                 SQD_TRY(launch_project_g(ctx, w.G, M, m, w.Z, M, r, w.GZ));
                 prof_end(ctx, 4.0 * m * r * dN, 8.0 * (2.0 * m + 4.0 * r) * dN);

@@ -1017,7 +1017,7 @@ __global__ void k_sum_partials(const double *__restrict__ partial, int nblk, int
     out[i] = s;
 }
 
-// in place: A_j[n] = sum_i A_i[n] Z[i + j*ldz] for j < r <= 4 (every element
+// in place: A_j[n] = sum_i A_i[n] Z[i + j*ldz] for j < r <= 8 (every element
 // is read by one thread before it writes, so the in-place update is safe)
 template <int R>
 __global__ void __launch_bounds__(256) k_combine_inplace(double *A, int64_t lda, int m,
@@ -1123,7 +1123,7 @@ int launch_dots_one(sqd_ctx *ctx, int MD, const double *V, int64_t ld, int m, co
 
 int launch_combine_inplace(sqd_ctx *ctx, double *A, int64_t lda, int m, const double *Z, int ldz,
                            int r, int64_t n) {
-    if (r < 1 || r > 4 || r > m)
+    if (r < 1 || r > 8 || r > m)
         return sqd_fail(ctx, SQD_EINVAL, "in-place combination of %d vectors", r);
     unsigned g = grid_1d(n, 256);
     if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
@@ -1132,7 +1132,11 @@ int launch_combine_inplace(sqd_ctx *ctx, double *A, int64_t lda, int m, const do
         case 1: k_combine_inplace<1><<<g, 256, 0, st>>>(A, lda, m, Z, ldz, n); break;
         case 2: k_combine_inplace<2><<<g, 256, 0, st>>>(A, lda, m, Z, ldz, n); break;
         case 3: k_combine_inplace<3><<<g, 256, 0, st>>>(A, lda, m, Z, ldz, n); break;
-        default: k_combine_inplace<4><<<g, 256, 0, st>>>(A, lda, m, Z, ldz, n); break;
+        case 4: k_combine_inplace<4><<<g, 256, 0, st>>>(A, lda, m, Z, ldz, n); break;
+        case 5: k_combine_inplace<5><<<g, 256, 0, st>>>(A, lda, m, Z, ldz, n); break;
+        case 6: k_combine_inplace<6><<<g, 256, 0, st>>>(A, lda, m, Z, ldz, n); break;
+        case 7: k_combine_inplace<7><<<g, 256, 0, st>>>(A, lda, m, Z, ldz, n); break;
+        default: k_combine_inplace<8><<<g, 256, 0, st>>>(A, lda, m, Z, ldz, n); break;
     }
     SQD_LAUNCHED(ctx);
     return SQD_OK;
