@@ -102,12 +102,11 @@ int sqd_build_strings(sqd_ctx *ctx, const uint64_t *d_raw, int64_t n_raw,
  * It allocates nothing: its scratch is a fixed 6.3 MB array in the
  * library's device memory, which every GPU that loads the library holds
  * until the process exits.  The caller passes the inputs and outputs exactly
- * as for sqd_build_strings, with the same result.
+ * as for sqd_build_strings (d_out may equal d_raw), with the same result.
  *  - n_raw may be at most 262144 (2^18); larger inputs return SQD_EINVAL
  *    (use sqd_build_strings).
  *  - The first call on a device looks up the array's device address on that
- *    device (cudaGetSymbolAddress); make that first call before any stream
- *    capture.
+ *    device (cudaGetSymbolAddress) and keeps it for later calls.
  *  - Every call shares the one array and leaves its contents behind: calls
  *    that overlap on the GPU (from several streams, threads or contexts) race
  *    and must be serialised by the caller.
