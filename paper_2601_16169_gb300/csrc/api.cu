@@ -647,10 +647,11 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
     dav_work w;
     // partial sums: multidot (M x nblk), block dot (nbd x M x k), Ritz (nbr x k),
     // preconditioner with Olsen's dots (2 x nbr + 2), fused passes (nbr x (MDf + 2))
+    // packed Gram of a block of up to 8 (nbr x 36)
     const int64_t npart = std::max<int64_t>(
         std::max<int64_t>(std::max<int64_t>((int64_t)M * nblk, (int64_t)nbd * M * k),
                           std::max<int64_t>((int64_t)nbr * std::max(k, 1), 2LL * nbr + 2)),
-        (int64_t)nbr * (MDf + 2));
+        std::max<int64_t>((int64_t)nbr * (MDf + 2), (int64_t)nbr * 36));
     SQD_TRY(dalloc(ctx, &w.Vb, (int64_t)M * N));
     SQD_TRY(dalloc(ctx, &w.Wb, (int64_t)M * N));
     SQD_TRY(dalloc(ctx, &w.X, (int64_t)k * N));
@@ -747,11 +748,23 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
         hZ.assign((size_t)b * b, 0.0);
         for (int round = 0; round < 2; round++) {
             prof_begin(ctx, PROF_ORTHO_BLOCK);
-            SQD_TRY(launch_block_dot(ctx, T, N, b, T, N, b, N, w.partial, nbd, w.P, b));
-            prof_end(ctx, 2.0 * b * b * dN, 16.0 * b * dN);
-            SQD_CUDA(ctx, cudaMemcpyAsync(hG.data(), w.P, sizeof(double) * b * b,
-                                          cudaMemcpyDeviceToHost, st));
-            SQD_CUDA(ctx, cudaStreamSynchronize(st));
+            if (b <= 8) {  // upper triangle only, unpacked on the host
+                SQD_TRY(launch_gram_tri(ctx, T, N, b, N, w.partial, nbr, w.P));
+                prof_end(ctx, 1.0 * b * (b + 1) * dN, 8.0 * b * dN);
+                double packed[36];
+                SQD_CUDA(ctx, cudaMemcpyAsync(packed, w.P, sizeof(double) * b * (b + 1) / 2,
+                                              cudaMemcpyDeviceToHost, st));
+                SQD_CUDA(ctx, cudaStreamSynchronize(st));
+                for (int j = 0; j < b; j++)
+                    for (int i = 0; i <= j; i++)
+                        hG[i + (size_t)j * b] = hG[j + (size_t)i * b] = packed[j * (j + 1) / 2 + i];
+            } else {
+                SQD_TRY(launch_block_dot(ctx, T, N, b, T, N, b, N, w.partial, nbd, w.P, b));
+                prof_end(ctx, 2.0 * b * b * dN, 16.0 * b * dN);
+                SQD_CUDA(ctx, cudaMemcpyAsync(hG.data(), w.P, sizeof(double) * b * b,
+                                              cudaMemcpyDeviceToHost, st));
+                SQD_CUDA(ctx, cudaStreamSynchronize(st));
+            }
             std::fill(hZ.begin(), hZ.end(), 0.0);
             std::vector<double> z(b), gz(b);
             for (int j = 0; j < b; j++) {
@@ -786,8 +799,8 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
             SQD_CUDA(ctx, cudaMemcpyAsync(Zd, hZ.data(), sizeof(double) * b * b,
                                           cudaMemcpyHostToDevice, st));
             prof_begin(ctx, PROF_ORTHO_BLOCK);
-            if (b <= 8) {
-                SQD_TRY(launch_combine_inplace(ctx, T, N, b, Zd, b, b, N));
+            if (b <= 8) {  // Z is upper triangular
+                SQD_TRY(launch_combine_tri(ctx, T, N, b, Zd, b, N));
             } else {
                 SQD_TRY(launch_combine(ctx, T, N, b, Zd, b, b, w.Tmp, N, N));
                 SQD_CUDA(ctx, cudaMemcpyAsync(T, w.Tmp, sizeof(double) * b * N,

@@ -980,6 +980,13 @@ struct mb_int {
         MB_CASE(12, f) MB_CASE(13, f) MB_CASE(14, f) MB_CASE(15, f)                          \
         default: f(mb_int<16>{}); break;                                                      \
     }
+// the same for m in [1, 8]
+#define MB8_DISPATCH(m, f)                                                                    \
+    switch (m) {                                                                              \
+        MB_CASE(1, f) MB_CASE(2, f) MB_CASE(3, f) MB_CASE(4, f) MB_CASE(5, f) MB_CASE(6, f)   \
+        MB_CASE(7, f)                                                                         \
+        default: f(mb_int<8>{}); break;                                                       \
+    }
 
 // V_i . x for i < MB (the new column of the projected matrix of a one-root
 // solve, x = W_new): every load of an element's MB basis values in flight at
@@ -1035,6 +1042,59 @@ __global__ void __launch_bounds__(256) k_combine_inplace(double *A, int64_t lda,
         }
 #pragma unroll
         for (int j = 0; j < R; j++) A[(int64_t)j * lda + p] = acc[j];
+    }
+}
+
+// Gram matrix of B vectors, upper triangle packed by columns:
+// partial[blk * CNT + j(j+1)/2 + i] = block blk's share of T_i . T_j, i <= j.
+// B(B+1)/2 multiply-adds per element, where a full B x B block dot does B^2.
+template <int B>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_gram_tri(const double *__restrict__ T, int64_t ld, int64_t n, double *__restrict__ partial) {
+    constexpr int CNT = B * (B + 1) / 2;
+    __shared__ double red[(RED_THREADS / 32) * CNT];
+    double acc[CNT];
+#pragma unroll
+    for (int c = 0; c < CNT; c++) acc[c] = 0.0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double t[B];
+#pragma unroll
+        for (int i = 0; i < B; i++) t[i] = T[(int64_t)i * ld + p];
+#pragma unroll
+        for (int j = 0; j < B; j++)
+#pragma unroll
+            for (int i = 0; i <= j; i++) acc[j * (j + 1) / 2 + i] = fma(t[i], t[j], acc[j * (j + 1) / 2 + i]);
+    }
+    int i;
+    double v;
+    if (block_sums<CNT>(acc, red, &i, &v)) partial[(int64_t)blockIdx.x * CNT + i] = v;
+}
+
+// in place T_j = sum_{i <= j} T_i Z[i + j*ldz], j < B, for an upper
+// triangular Z (the coefficients of Gram-Schmidt on the Gram matrix)
+template <int B>
+__global__ void __launch_bounds__(256) k_combine_tri(double *T, int64_t ld,
+                                                     const double *__restrict__ Z, int ldz,
+                                                     int64_t n) {
+    constexpr int CNT = B * (B + 1) / 2;
+    double z[CNT];
+#pragma unroll
+    for (int j = 0; j < B; j++)
+#pragma unroll
+        for (int i = 0; i <= j; i++) z[j * (j + 1) / 2 + i] = __ldg(Z + i + (int64_t)j * ldz);
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double t[B];
+#pragma unroll
+        for (int i = 0; i < B; i++) t[i] = T[(int64_t)i * ld + p];
+#pragma unroll
+        for (int j = 0; j < B; j++) {
+            double a = 0.0;
+#pragma unroll
+            for (int i = 0; i <= j; i++) a = fma(t[i], z[j * (j + 1) / 2 + i], a);
+            T[(int64_t)j * ld + p] = a;
+        }
     }
 }
 
@@ -1138,6 +1198,40 @@ int launch_combine_inplace(sqd_ctx *ctx, double *A, int64_t lda, int m, const do
         case 7: k_combine_inplace<7><<<g, 256, 0, st>>>(A, lda, m, Z, ldz, n); break;
         default: k_combine_inplace<8><<<g, 256, 0, st>>>(A, lda, m, Z, ldz, n); break;
     }
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// out[j(j+1)/2 + i] = T_i . T_j for i <= j < b <= 8; partial: nblk * b(b+1)/2
+int launch_gram_tri(sqd_ctx *ctx, const double *T, int64_t ld, int b, int64_t n, double *partial,
+                    int nblk, double *out) {
+    if (b < 1 || b > 8) return sqd_fail(ctx, SQD_EINVAL, "packed Gram matrix of %d vectors", b);
+    cudaStream_t st = ctx->stream;
+    auto go = [&](auto mb) {
+        constexpr int B = decltype(mb)::value;
+        k_gram_tri<B><<<nblk, RED_THREADS, 0, st>>>(T, ld, n, partial);
+    };
+    MB8_DISPATCH(b, go);
+    SQD_LAUNCHED(ctx);
+    const int cnt = b * (b + 1) / 2;
+    k_sum_partials<<<1, 64, 0, st>>>(partial, nblk, cnt, cnt, out);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// in place T_j = sum_{i <= j} T_i Z[i + j*ldz], j < b <= 8 (Z upper triangular)
+int launch_combine_tri(sqd_ctx *ctx, double *T, int64_t ld, int b, const double *Z, int ldz,
+                       int64_t n) {
+    if (b < 1 || b > 8)
+        return sqd_fail(ctx, SQD_EINVAL, "triangular combination of %d vectors", b);
+    unsigned g = grid_1d(n, 256);
+    if (g > 8u * (unsigned)ctx->sm_count * 8u) g = 8u * (unsigned)ctx->sm_count * 8u;
+    cudaStream_t st = ctx->stream;
+    auto go = [&](auto mb) {
+        constexpr int B = decltype(mb)::value;
+        k_combine_tri<B><<<g, 256, 0, st>>>(T, ld, Z, ldz, n);
+    };
+    MB8_DISPATCH(b, go);
     SQD_LAUNCHED(ctx);
     return SQD_OK;
 }

@@ -281,6 +281,10 @@ int launch_gs_update_scale(sqd_ctx *, int MD, const double *V, int64_t ld, int m
                            const double *P, double scale, double *T, int64_t n, int nblk);
 int launch_combine_inplace(sqd_ctx *, double *A, int64_t lda, int m, const double *Z, int ldz,
                            int r, int64_t n);
+int launch_gram_tri(sqd_ctx *, const double *T, int64_t ld, int b, int64_t n, double *partial,
+                    int nblk, double *out);
+int launch_combine_tri(sqd_ctx *, double *T, int64_t ld, int b, const double *Z, int ldz,
+                       int64_t n);
 int launch_dots_one(sqd_ctx *, int MD, const double *V, int64_t ld, int m, const double *x,
                     int64_t n, double *partial, int nblk, double *out);
 int launch_project_coeffs(sqd_ctx *, const double *Z, int ldz, int m, int r, const double *Pold,
