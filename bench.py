@@ -61,7 +61,7 @@ DESCR = {
     "adjoint29": "adjoint29: norb=29, 5+5 electrons, 5000 shared strings, 2.5e7 determinants",
     "full8": "full8: norb=8, 4+4 electrons, full space, 4900 determinants",
 }
-SUBRECORDS = ("h2o29", "df", "batched", "adjoint", "stored")
+SUBRECORDS = ("h2o29", "full8", "df", "batched", "adjoint", "stored")
 
 # FP64 peak for the ALU roofline: 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM
 # (the nominal 1.25 TFLOP/s FP64 of GB300 at its maximum SM clock).
@@ -642,8 +642,8 @@ def headline(args, rank, world, local_rank):
         for name in subs:
             if name == "df":
                 continue
-            fn = {"h2o29": sub_h2o29, "batched": sub_batched, "adjoint": sub_adjoint,
-                  "stored": sub_stored}[name]
+            fn = {"h2o29": sub_h2o29, "full8": sub_full8, "batched": sub_batched,
+                  "adjoint": sub_adjoint, "stored": sub_stored}[name]
             try:
                 line[name] = fn(args, local_rank)
             except Exception as exc:  # a failed sub-record is reported, not fatal
@@ -750,8 +750,9 @@ def run_solve(args, rank, world, local_rank, steps=None, warmup=None, e2e_steps=
         "clocks": clocks, "gpu_launches": launches}
     if with_cpu and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(w, args.cpu_rows or default_cpu_rows(args.workload))
+        rows_1t = max(1000, (args.cpu_rows or default_cpu_rows(args.workload)) // 100)
         out["cpu_baseline_1thread"] = cpu_baseline_one_thread(
-            args.workload, max(1000, (args.cpu_rows or default_cpu_rows(args.workload)) // 100))
+            args.workload, w.ndet if w.ndet <= 10000 else rows_1t)
     return out
 
 
@@ -998,6 +999,58 @@ def sub_h2o29(args, local_rank):
             "sigma_share_of_step", "sigma_bound", "roofline", "davidson_classes", "kernel_ms",
             "e2e", "clocks", "cpu_baseline", "cpu_baseline_1thread", "config")
     return {k: r[k] for k in keep if k in r}
+
+
+def oracle_solve(name):
+    """The whole oracle solve of a small workload on the host cores: the
+    diagonal, then the oracle's Davidson with its matrix-free sigma, under
+    the same options as the device solve."""
+    import oracle
+    w = si.workload(name)
+    o = SOLVE[name]
+    t0 = time.perf_counter()
+    hd = oracle.diag(w.norb, w.h, w.V, 0.0, w.strings_a, w.strings_b)
+    th, _, it, _, conv = oracle.davidson(
+        lambda X: oracle.sigma(w.norb, w.h, w.V, 0.0, w.strings_a, w.strings_b, X.T).T, hd,
+        nroots=o["nroots"], tol_residual=o["tol_residual"], tol_energy=o["tol_energy"],
+        max_iter=o["max_iter"])
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": "solves/s", "cores": _cores(), "kind": "oracle",
+            "sample": "the whole oracle solve of %s (diagonal + Davidson, %d iterations), "
+                      "not extrapolated" % (name, int(it)),
+            "seconds": dt, "energies": [float(x) for x in th], "converged": bool(conv)}
+
+
+def oracle_solve_one_thread(name):
+    """oracle_solve on one host thread (a child process with OMP_NUM_THREADS=1)."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_solve(%r)))" % (ROOT, name))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True,
+                             text=True, timeout=300)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as exc:  # reported, not fatal
+        return {"error": str(exc)[:200]}
+
+
+def sub_full8(args, local_rank):
+    """The 4900-determinant full space (8 orbitals, 4+4 electrons): the whole
+    device path per step against the whole oracle solve, on all host cores
+    and on one thread."""
+    a = _sub_args(args, workload="full8", steps=20, warmup=3)
+    r = run_solve(a, 0, 1, local_rank, e2e_steps=5)
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "time_to_converged_E_s",
+            "davidson_iterations", "energy", "e2e", "clocks", "cpu_baseline",
+            "cpu_baseline_1thread", "config")
+    out = {k: r[k] for k in keep if k in r}
+    if not args.no_cpu_baseline:
+        so = oracle_solve("full8")
+        out["cpu_baseline_solve"] = so
+        out["cpu_baseline_solve_1thread"] = oracle_solve_one_thread("full8")
+        out["abs_energy_diff_vs_oracle"] = abs(float(r["energy"]) - so["energies"][0])
+        out["solve_speedup_vs_oracle"] = so["seconds"] / (r["ms_per_step"] / 1e3)
+    return out
 
 
 def sub_batched(args, local_rank):

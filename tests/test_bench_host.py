@@ -47,3 +47,13 @@ def test_class_record_fractions():
     assert abs(r["tflops"] - 1.0) < 1e-12
     assert abs(r["frac_fp64_peak"] - 1.0 / bench.FP64_PEAK_TFLOPS) < 1e-12
     assert abs(r["gbs"] - 3300.0) < 1e-9
+
+
+def test_oracle_solve_baseline_full8():
+    # the whole-solve CPU baseline of the full8 sub-record reaches the stored
+    # lowest eigenvalue of the dense full8 Hamiltonian
+    from tests.golden import make_golden as mg
+    r = bench.oracle_solve("full8")
+    assert r["converged"] and r["kind"] == "oracle" and r["seconds"] > 0
+    assert abs(r["energies"][0] - mg.read_full8()[0]) <= 1e-9
+    assert "full8" in bench.SUBRECORDS
