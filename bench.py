@@ -61,7 +61,7 @@ DESCR = {
     "adjoint29": "adjoint29: norb=29, 5+5 electrons, 5000 shared strings, 2.5e7 determinants",
     "full8": "full8: norb=8, 4+4 electrons, full space, 4900 determinants",
 }
-SUBRECORDS = ("h2o29", "full8", "df", "batched", "adjoint", "stored")
+SUBRECORDS = ("h2o29", "full8", "df", "spin_flip", "batched", "adjoint", "stored")
 
 # FP64 peak for the ALU roofline: 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM
 # (the nominal 1.25 TFLOP/s FP64 of GB300 at its maximum SM clock).
@@ -102,6 +102,9 @@ def _args(argv=None):
                    help="batched mode: residual tolerance of both solvers")
     p.add_argument("--sigma-mode", type=int, default=0, choices=[0, 1],
                    help="0: native FP64 sigma (headline); 1: double-float on the FP32 pipe")
+    p.add_argument("--spin-flip", type=int, default=0, choices=[-1, 0, 1],
+                   help="sigma/solve modes: vectors of one spin-flip sector (C^T = s C, "
+                        "shared string sets only); 0: general vectors")
     p.add_argument("--correction", default="davidson", choices=["davidson", "olsen"],
                    help="Davidson correction vector (olsen: orthogonal to the Ritz vector)")
     p.add_argument("--max-iter", type=int, default=None,
@@ -643,7 +646,9 @@ def headline(args, rank, world, local_rank):
             if name == "df":
                 continue
             fn = {"h2o29": sub_h2o29, "full8": sub_full8, "batched": sub_batched,
-                  "adjoint": sub_adjoint, "stored": sub_stored}[name]
+                  "adjoint": sub_adjoint, "stored": sub_stored}.get(name)
+            if name == "spin_flip":
+                fn = lambda a, lr: sub_spin_flip(a, lr, line.get("energy"))  # noqa: E731
             try:
                 line[name] = fn(args, local_rank)
             except Exception as exc:  # a failed sub-record is reported, not fatal
@@ -686,6 +691,8 @@ def run_solve(args, rank, world, local_rank, steps=None, warmup=None, e2e_steps=
         t = env.tables(w, raw, h, V)
         if args.sigma_mode:
             t.set_sigma_mode(args.sigma_mode)
+        if getattr(args, "spin_flip", 0):
+            t.set_spin_flip(args.spin_flip)
         e, C, it, res, rc = sqd.davidson(ctx, t, **opts)
         t.close()
         del C
@@ -764,6 +771,10 @@ def run_sigma_only(args, rank, world, local_rank):
     w = si.workload(args.workload)
     t = env.tables(w)
     C = env.tensor(si.random_vectors(1, w.ndet, 13).reshape(w.strings_a.size, w.strings_b.size))
+    sflip = getattr(args, "spin_flip", 0)
+    if sflip:  # a vector of the sector
+        C = C + sflip * C.T
+        t.set_spin_flip(sflip)
     S = torch.empty_like(C)
     if getattr(args, "sigma_mode", 0):
         t.set_sigma_mode(args.sigma_mode)
@@ -791,7 +802,8 @@ def run_sigma_only(args, rank, world, local_rank):
     env.close()
     if rank != 0:
         return None
-    out = {"mode": "sigma", "sigma_mode": getattr(args, "sigma_mode", 0), "metric": METRIC,
+    out = {"mode": "sigma", "sigma_mode": getattr(args, "sigma_mode", 0),
+           "spin_flip": getattr(args, "spin_flip", 0), "metric": METRIC,
            "value": args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "dtype": "f64",
@@ -1050,6 +1062,52 @@ def sub_full8(args, local_rank):
         out["cpu_baseline_solve_1thread"] = oracle_solve_one_thread("full8")
         out["abs_energy_diff_vs_oracle"] = abs(float(r["energy"]) - so["energies"][0])
         out["solve_speedup_vs_oracle"] = so["seconds"] / (r["ms_per_step"] / 1e3)
+    return out
+
+
+# spin-flip sector of the singlets: with the alpha-first determinant
+# ordering a state of total spin S has C^T = (-1)^S C
+SINGLET_SECTOR = 1
+
+
+def sub_spin_flip(args, local_rank, e_general=None):
+    """The default workload in the singlet spin-flip sector (C^T = C, one
+    same-spin pass per sigma): sigma steps on a vector of the sector, then
+    the lowest singlet-sector state, its energy beside the general solve's
+    (equal when the ground state is a singlet)."""
+    env = Env(local_rank)
+    torch = env.torch
+    w = si.workload(args.workload)
+    sector = SINGLET_SECTOR
+    t = env.tables(w)
+    t.set_spin_flip(sector)
+    n = w.strings_a.size
+    C = env.tensor(si.random_vectors(1, w.ndet, 13).reshape(n, n))
+    C = C + sector * C.T
+    S = torch.empty_like(C)
+    steps = max(3, min(args.steps, 10))
+    dev_ms, prof, launches, clocks = sigma_steps(env, t, C, S, steps, 2)
+    del C, S
+    torch.cuda.empty_cache()
+    sig = sigma_summary(prof)
+    out = {"sector": sector, "value": steps / (dev_ms / 1e3), "unit": UNIT,
+           "ms_per_step": dev_ms / steps, "steps": steps,
+           "note": "sigma = T + s T^T + H_II C + sigma_ab on vectors with C^T = s C: one "
+                   "same-spin pass; the general line forms both",
+           "sigma_bound": sig["bound"], "roofline": sigma_roofline(prof, args.workload),
+           "kernels": class_record(prof, SIGMA_CLASSES), "clocks": clocks,
+           "gpu_launches": launches}
+    if not args.no_solve:
+        sr = solve_record(env, t, dict(SOLVE[args.workload]), args.workload)
+        out["time_to_converged_E_s"] = sr["time_to_converged_E_s"]
+        out["davidson_iterations"] = sr["iterations"]
+        out["energy"] = sr["energies"][0]
+        out["residual"] = sr["residuals"][0]
+        out["solve"] = sr
+        if e_general is not None:
+            out["abs_energy_diff_vs_general_solve"] = abs(sr["energies"][0] - e_general)
+    t.close()
+    env.close()
     return out
 
 

@@ -233,6 +233,36 @@ int sqd_map_vector(sqd_ctx *ctx, const uint64_t *d_old_a, int64_t n_old_a,
  */
 int sqd_tables_set_sigma_mode(sqd_tables *tables, int mode);
 
+/*
+ * Spin-flip sectors (sector = +1 or -1; 0, the default, turns it off).
+ * Only for tables built with one string set for both spins (the same device
+ * array and electron count); otherwise SQD_EINVAL.
+ *
+ * With a shared string set, exchanging the alpha and beta strings of every
+ * determinant, (Ia, Ib) -> (Ib, Ia), commutes with H (Section II's
+ * Hamiltonian is spin-free and (pq|rs) = (rs|pq)), so the vectors, as
+ * n x n matrices, split into a symmetric sector (C^T = C) and an
+ * antisymmetric one (C^T = -C).  With this determinant ordering (all alpha
+ * operators before the beta ones) an eigenstate of total spin S lies in
+ * sector (-1)^S, whatever the electron count: singlets in +1, triplets in
+ * -1.  On a vector of sector s the beta-beta part of sigma is
+ * s times the transpose of the alpha-alpha part, so with sector s set:
+ *  - sqd_sigma forms sigma = T + s T^T + H_II C + sigma_ab(C) with
+ *    T = sigma_aa(C): one same-spin pass instead of two.  The caller states
+ *    that every input vector lies in sector s; for any other vector the
+ *    result is not H C.
+ *  - sqd_davidson searches sector s: its guess vectors are the sector's unit
+ *    vectors e_II or (e_IJ + s e_JI)/sqrt(2) on the lowest H_II with
+ *    Ia <= Ib (Ia < Ib for s = -1), or the caller's guess projected on the
+ *    sector, and every correction vector is projected, (X + s X^T)/2,
+ *    before it is orthogonalised, so the basis stays exactly in the sector.
+ *    Its roots are the lowest of that sector, not necessarily of H.
+ * Applies to the FP64 products (sigma mode 0); not to the batched solver,
+ * the stored-H product or the RDMs.  Not in the paper, which forms the
+ * three parts of sigma on every vector.
+ */
+int sqd_tables_set_spin_flip(sqd_tables *tables, int sector);
+
 /* ------------------------------------------------ stored-H variant -- */
 
 /*

@@ -51,6 +51,7 @@ EXPORTED = [
     "sqd_batched_tuning_buckets", "sqd_batched_set_tile",
     "sqd_stored_h_build", "sqd_sigma_stored", "sqd_string_weights", "sqd_select_strings",
     "sqd_map_vector", "sqd_tables_set_sigma_mode", "sqd_measure_fp64_peaks",
+    "sqd_tables_set_spin_flip",
 ]
 
 PROFILE_CLASSES = ["same_spin_alpha", "same_spin_beta", "alpha_beta", "transpose", "tables",
@@ -126,6 +127,7 @@ def lib():
     L.sqd_map_vector.argtypes = [vp, vp, i64, vp, i64, vp, vp, i64, vp, i64, vp,
                                  ctypes.POINTER(dbl)]
     L.sqd_tables_set_sigma_mode.argtypes = [vp, i32]
+    L.sqd_tables_set_spin_flip.argtypes = [vp, i32]
     L.sqd_measure_fp64_peaks.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     _LIB = L
     return L
@@ -237,6 +239,12 @@ class Tables:
         """sqd_tables_set_sigma_mode: 0 native FP64, 1 double-float on the
         FP32 pipe (sigma and Davidson on these tables)."""
         self.ctx._check(self.ctx._lib.sqd_tables_set_sigma_mode(self.handle, int(mode)))
+
+    def set_spin_flip(self, sector: int):
+        """sqd_tables_set_spin_flip: +1 / -1 for vectors with C^T = sector * C
+        (sigma with one same-spin pass, Davidson in that sector); 0 for
+        general vectors.  Shared string sets only."""
+        self.ctx._check(self.ctx._lib.sqd_tables_set_spin_flip(self.handle, int(sector)))
 
     def export(self, spin: int, kind: int) -> dict:
         """Host (numpy) copy of one excitation table: off, tgt, orb, sign, val."""

@@ -440,6 +440,18 @@ int sqd_tables_set_sigma_mode(sqd_tables *t, int mode) {
     return SQD_OK;
 }
 
+int sqd_tables_set_spin_flip(sqd_tables *t, int sector) {
+    if (!t) return fail_noctx(SQD_EINVAL, "sqd_tables_set_spin_flip: tables is NULL");
+    if (sector < -1 || sector > 1)
+        return fail_noctx(SQD_EINVAL, "spin-flip sector must be -1, 0 or +1");
+    if (sector && !t->shared)
+        return fail_noctx(SQD_EINVAL,
+                          "spin flip needs one string set shared by both spins (the same "
+                          "device array and electron count)");
+    t->spin_flip = sector;
+    return SQD_OK;
+}
+
 int sqd_tables_info(const sqd_tables *t, int64_t *info) {
     if (!t || !info) return fail_noctx(SQD_EINVAL, "sqd_tables_info: NULL argument");
     info[0] = t->norb;
@@ -548,6 +560,23 @@ static int sigma_impl(sqd_ctx *ctx, sqd_tables *t, const double *C, double *S, i
         return SQD_OK;
     }
     SQD_TRY(tune_ab_groups(ctx, t, 0, ab_launch_fp64, C));
+    if (t->spin_flip) {
+        // C^T = s C: sigma = T + s T^T + H_II C + sigma_ab, T the alpha side
+        for (int v = 0; v < nvec; v++) {
+            const double *Cv = C + (int64_t)v * N;
+            double *Sv = S + (int64_t)v * N;
+            prof_begin(ctx, PROF_SAME_ALPHA);
+            SQD_TRY(launch_same_spin(ctx, &t->a, t->b, na, nb, Cv, t->scratch_s, nullptr));
+            prof_end(ctx, f_a - 2.0 * (double)N, 2 * vb);
+            prof_begin(ctx, PROF_TRANSPOSE);
+            SQD_TRY(launch_sym_combine(ctx, t->spin_flip, t->scratch_s, t->diag, Cv, Sv, na));
+            prof_end(ctx, 2.0 * (double)N, 5 * vb);
+            prof_begin(ctx, PROF_ALPHA_BETA);
+            SQD_TRY(launch_alpha_beta(ctx, t, Cv, Sv));
+            prof_end(ctx, f_ab, 3 * vb);
+        }
+        return SQD_OK;
+    }
     for (int v = 0; v < nvec; v++) {
         const double *Cv = C + (int64_t)v * N;
         double *Sv = S + (int64_t)v * N;
@@ -849,16 +878,32 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
         return within_block(m0, b, nacc);
     };
 
+    // spin flip: every basis vector is kept exactly in the sector
+    // (C^T = s C), so the solve stays there whatever the rounding
+    const int sflip = t->spin_flip;
+    const int64_t nsym = sflip ? t->a.n : 0;
+    auto symmetrize = [&](double *X, int cnt) -> int {
+        if (!nsym) return SQD_OK;
+        prof_begin(ctx, PROF_DAVIDSON);
+        for (int q = 0; q < cnt; q++)
+            SQD_TRY(launch_symmetrize(ctx, sflip, X + (int64_t)q * N, nsym));
+        prof_end(ctx, 1.0 * cnt * dN, 32.0 * cnt * dN);
+        return SQD_OK;
+    };
     int m = 0;
     if (o->use_guess) {
         SQD_CUDA(ctx, cudaMemcpyAsync(w.Vb, d_C, sizeof(double) * k * N, cudaMemcpyDeviceToDevice,
                                       st));
+        SQD_TRY(symmetrize(w.Vb, k));
         SQD_TRY(orthonormalize_block(0, k, false, &m));
         if (m < k) return sqd_fail(ctx, SQD_EINVAL, "initial guess vectors are linearly dependent");
     } else {
         SQD_CUDA(ctx, cudaMemsetAsync(w.Vb, 0, sizeof(double) * k * N, st));
-        SQD_TRY(launch_argmin_k(ctx, t->diag, N, k, w.idx));
-        SQD_TRY(launch_set_unit(ctx, w.Vb, N, k, w.idx));
+        SQD_TRY(launch_argmin_k(ctx, t->diag, N, k, w.idx, sflip < 0 ? -nsym : nsym));
+        if (nsym)
+            SQD_TRY(launch_set_unit_sym(ctx, w.Vb, N, k, w.idx, nsym, sflip));
+        else
+            SQD_TRY(launch_set_unit(ctx, w.Vb, N, k, w.idx));
         m = k;
     }
     auto apply_h = [&](const double *Cin, double *Sout, int nv) -> int {
@@ -937,6 +982,8 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
             SQD_TRY(launch_ritz_prec_dot(ctx, MDf, w.Vb, w.Wb, N, m, w.evecs, w.evals, t->diag,
                                          o->precond_floor, N, T, w.partial, nbr, s1));
             prof_end(ctx, (6.0 * m + 7.0) * dN, 8.0 * (2.0 * m + 3.0) * dN);
+            // (V^T t is unchanged by the symmetrisation: V is symmetric)
+            SQD_TRY(symmetrize(T, 1));
             SQD_CUDA(ctx, cudaMemcpyAsync(hs, s1 + m, sizeof(double) * 2, cudaMemcpyDeviceToHost,
                                           st));
             SQD_CUDA(ctx, cudaMemcpyAsync(theta.data(), w.evals, sizeof(double),
@@ -1132,6 +1179,7 @@ static int davidson_impl(sqd_ctx *ctx, sqd_tables *t, const sqd_options *o, doub
                                                      w.tn2 + q));
             }
             prof_end(ctx, 2.0 * b * dN, 24.0 * b * dN);
+            SQD_TRY(symmetrize(w.Vb + (int64_t)m_old * N, b));
             int nacc = 0;
             SQD_TRY(orthonormalize_block(m_old, b, true, &nacc));
             m = m_old + nacc;

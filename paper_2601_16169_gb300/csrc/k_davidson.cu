@@ -644,13 +644,16 @@ __device__ __forceinline__ bool vi_less(double v1, int64_t i1, double v2, int64_
 
 __global__ void __launch_bounds__(RED_THREADS)
     k_argmin_partial(const double *__restrict__ d, int64_t n, double lv, int64_t li,
-                     double *__restrict__ pv, int64_t *__restrict__ pi) {
+                     int64_t sym_n, double *__restrict__ pv, int64_t *__restrict__ pi) {
     __shared__ double sv[RED_THREADS];
     __shared__ int64_t si[RED_THREADS];
     double bv = INFINITY;
     int64_t bi = -1;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
+        // sym_n > 0: only I <= J of an sym_n x sym_n matrix; < 0: only I < J
+        if (sym_n > 0 && p / sym_n > p % sym_n) continue;
+        if (sym_n < 0 && p / (-sym_n) >= p % (-sym_n)) continue;
         double v = d[p];
         bool after = (li < 0) || vi_less(lv, li, v, p);
         if (after && (bi < 0 || vi_less(v, p, bv, bi))) {
@@ -691,7 +694,8 @@ __global__ void k_argmin_final(const double *pv, const int64_t *pi, int nblk, in
     lastv[0] = bv;
 }
 
-int launch_argmin_k(sqd_ctx *ctx, const double *d, int64_t n, int k, int64_t *idx_dev) {
+int launch_argmin_k(sqd_ctx *ctx, const double *d, int64_t n, int k, int64_t *idx_dev,
+                    int64_t sym_n) {
     int nblk = 4 * ctx->sm_count;
     double *pv = nullptr, *lastv = nullptr;
     int64_t *pi = nullptr;
@@ -701,7 +705,7 @@ int launch_argmin_k(sqd_ctx *ctx, const double *d, int64_t n, int k, int64_t *id
     double hv = 0.0;
     int64_t hi = -1;
     for (int t = 0; t < k; t++) {
-        k_argmin_partial<<<nblk, RED_THREADS, 0, ctx->stream>>>(d, n, hv, hi, pv, pi);
+        k_argmin_partial<<<nblk, RED_THREADS, 0, ctx->stream>>>(d, n, hv, hi, sym_n, pv, pi);
         SQD_LAUNCHED(ctx);
         k_argmin_final<<<1, 1, 0, ctx->stream>>>(pv, pi, nblk, t, idx_dev, lastv);
         SQD_LAUNCHED(ctx);
@@ -724,6 +728,29 @@ __global__ void k_set_unit(double *V, int64_t ld, int k, const int64_t *idx) {
 
 int launch_set_unit(sqd_ctx *ctx, double *V, int64_t ld, int k, const int64_t *idx_dev) {
     k_set_unit<<<1, 128, 0, ctx->stream>>>(V, ld, k, idx_dev);
+    SQD_LAUNCHED(ctx);
+    return SQD_OK;
+}
+
+// the normalised unit vectors of one spin-flip sector at positions (I, J),
+// I <= J, of an n x n matrix: e_II (sgn = +1 only), or
+// (e_IJ + sgn e_JI) / sqrt(2)
+__global__ void k_set_unit_sym(double *V, int64_t ld, int k, const int64_t *idx, int64_t n,
+                               int sgn) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= k) return;
+    const int64_t p = idx[j], I = p / n, J = p % n;
+    if (I == J) {
+        V[(int64_t)j * ld + p] = 1.0;
+    } else {
+        V[(int64_t)j * ld + p] = M_SQRT1_2;
+        V[(int64_t)j * ld + J * n + I] = sgn > 0 ? M_SQRT1_2 : -M_SQRT1_2;
+    }
+}
+
+int launch_set_unit_sym(sqd_ctx *ctx, double *V, int64_t ld, int k, const int64_t *idx_dev,
+                        int64_t n, int sgn) {
+    k_set_unit_sym<<<1, 128, 0, ctx->stream>>>(V, ld, k, idx_dev, n, sgn);
     SQD_LAUNCHED(ctx);
     return SQD_OK;
 }

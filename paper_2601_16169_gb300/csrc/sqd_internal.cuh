@@ -148,6 +148,10 @@ struct sqd_tables {
     int64_t *rdm_chunks = nullptr, *rdm_groups = nullptr;
     // double-float sigma mode (0: FP64, 1: df32)
     int sigma_mode = 0;
+    // +1 / -1: C^T = spin_flip * C asserted by the caller (shared string
+    // set): the beta side of sigma is the alpha side transposed times the
+    // sign; Davidson searches that sector.  0: general vectors.
+    int spin_flip = 0;
     bool df_ready = false;
     float2 *Vf = nullptr, *diagf = nullptr;
     double *scratch_c = nullptr;  // C as float pairs (8 bytes per element)
@@ -264,8 +268,17 @@ int launch_scale(sqd_ctx *, double *x, int64_t n, const double *s_dev, int inver
 int launch_jacobi_eigh(sqd_ctx *, const double *G, int ldg, int m, double *evals, double *evecs,
                        int m_old = 0, const double *E_old = nullptr,
                        const double *th_old = nullptr);
-int launch_argmin_k(sqd_ctx *, const double *d, int64_t n, int k, int64_t *idx_dev);
+// sym_n > 0: only positions (I, J) with I <= J of an sym_n x sym_n matrix;
+// sym_n < 0: only I < J of a (-sym_n) x (-sym_n) matrix
+int launch_argmin_k(sqd_ctx *, const double *d, int64_t n, int k, int64_t *idx_dev,
+                    int64_t sym_n = 0);
 int launch_set_unit(sqd_ctx *, double *V, int64_t ld, int k, const int64_t *idx_dev);
+int launch_set_unit_sym(sqd_ctx *, double *V, int64_t ld, int k, const int64_t *idx_dev,
+                        int64_t n, int sgn);
+// spin-flip sector pieces (n x n vectors of a shared string set, C^T = sgn C)
+int launch_sym_combine(sqd_ctx *, int sgn, const double *T, const double *D, const double *C,
+                       double *S, int64_t n);
+int launch_symmetrize(sqd_ctx *, int sgn, double *X, int64_t n);
 int launch_fix_phase(sqd_ctx *, double *X, int64_t ld, int k, int64_t n, double *work_dev);
 int launch_gdk_basis(sqd_ctx *, const double *Y, int m, int m2, const double *P, int mp, int k,
                      int ldp, double *Z, int ldz, int *r_dev);
