@@ -427,7 +427,7 @@ void sqd_free_tables(sqd_tables *t) {
                     t->ab.group_rows, t->scratch_t, t->scratch_s, t->rdm_iket,
                     t->rdm_ibra,  t->rdm_ipq,    t->rdm_chunks, t->rdm_groups,
                     t->st_rowptr, t->st_col,     t->st_val,  t->Vf,
-                    t->diagf,     t->scratch_c};
+                    t->diagf,     t->scratch_c, t->scratch_h};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete t;
@@ -561,7 +561,12 @@ static int sigma_impl(sqd_ctx *ctx, sqd_tables *t, const double *C, double *S, i
     }
     SQD_TRY(tune_ab_groups(ctx, t, 0, ab_launch_fp64, C));
     if (t->spin_flip) {
-        // C^T = s C: sigma = T + s T^T + H_II C + sigma_ab, T the alpha side
+        // C^T = s C: sigma = (T + s T^T) + H_II C + (Y + s Y^T) with T the
+        // alpha side and Y the paired singles of the upper triangle Ch
+        const int s = t->spin_flip;
+        if (!t->scratch_h) SQD_TRY(dalloc(ctx, &t->scratch_h, N, &t->bytes));
+        double fu = 0.0;
+        SQD_TRY(alpha_beta_upper_work(ctx, t, &fu));
         for (int v = 0; v < nvec; v++) {
             const double *Cv = C + (int64_t)v * N;
             double *Sv = S + (int64_t)v * N;
@@ -569,11 +574,15 @@ static int sigma_impl(sqd_ctx *ctx, sqd_tables *t, const double *C, double *S, i
             SQD_TRY(launch_same_spin(ctx, &t->a, t->b, na, nb, Cv, t->scratch_s, nullptr));
             prof_end(ctx, f_a - 2.0 * (double)N, 2 * vb);
             prof_begin(ctx, PROF_TRANSPOSE);
-            SQD_TRY(launch_sym_combine(ctx, t->spin_flip, t->scratch_s, t->diag, Cv, Sv, na));
-            prof_end(ctx, 2.0 * (double)N, 5 * vb);
+            SQD_TRY(launch_upper_half(ctx, s, Cv, t->scratch_h, na));
+            SQD_CUDA(ctx, cudaMemsetAsync(t->scratch_t, 0, sizeof(double) * N, ctx->stream));
+            prof_end(ctx, 0.0, 3 * vb);
             prof_begin(ctx, PROF_ALPHA_BETA);
-            SQD_TRY(launch_alpha_beta(ctx, t, Cv, Sv));
-            prof_end(ctx, f_ab, 3 * vb);
+            SQD_TRY(launch_alpha_beta_upper(ctx, t, t->scratch_h, t->scratch_t));
+            prof_end(ctx, 2.0 * fu, 3 * vb);
+            prof_begin(ctx, PROF_TRANSPOSE);
+            SQD_TRY(launch_sym_combine(ctx, s, t->scratch_s, t->scratch_t, t->diag, Cv, Sv, na));
+            prof_end(ctx, 2.0 * (double)N, 6 * vb);
         }
         return SQD_OK;
     }

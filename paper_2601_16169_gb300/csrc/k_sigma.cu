@@ -140,91 +140,3 @@ int launch_transpose(sqd_ctx *ctx, const double *in, double *out, int64_t rows, 
     SQD_LAUNCHED(ctx);
     return SQD_OK;
 }
-
-// ----------------------------------------------------------- spin flip --
-// For a shared string set the exchange of the alpha and beta strings,
-// (Ia, Ib) -> (Ib, Ia), commutes with H: the two same-spin tables, the
-// couplings W and the diagonal are the same for both spins, and
-// (pq|rs) = (rs|pq).  On a vector of one sector, C^T = s C with s = +1 or -1,
-// the beta side is the alpha side transposed times s,
-//   sigma = T + s T^T + H_II C + sigma_ab(C),   T = sigma_aa(C) (no diagonal).
-
-// S[r][c] = T[r][c] + s T[c][r] + D[r][c] C[r][c] for one 32 x 32 tile; n x n
-template <int SGN>
-__global__ void k_sym_combine(const double *__restrict__ T, const double *__restrict__ D,
-                              const double *__restrict__ C, double *__restrict__ S, int64_t n) {
-    __shared__ double tile[32][33];
-    const int64_t c0 = (int64_t)blockIdx.x * 32;
-    for (int64_t r0 = (int64_t)blockIdx.y * 32; r0 < n; r0 += (int64_t)gridDim.y * 32) {
-        // tile[i][x] = T[c0 + i][r0 + x] (rows of the mirrored tile, coalesced)
-        for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-            const int64_t c = c0 + i, r = r0 + threadIdx.x;
-            if (c < n && r < n) tile[i][threadIdx.x] = T[c * n + r];
-        }
-        __syncthreads();
-        for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-            const int64_t r = r0 + i, c = c0 + threadIdx.x;
-            if (r < n && c < n) {
-                const int64_t p = r * n + c;
-                const double m = tile[threadIdx.x][i];
-                S[p] = (SGN > 0 ? T[p] + m : T[p] - m) + D[p] * C[p];
-            }
-        }
-        __syncthreads();
-    }
-}
-
-int launch_sym_combine(sqd_ctx *ctx, int sgn, const double *T, const double *D, const double *C,
-                       double *S, int64_t n) {
-    if (n == 0) return SQD_OK;
-    if (sgn != 1 && sgn != -1) return sqd_fail(ctx, SQD_EINVAL, "sector must be +1 or -1");
-    const int64_t g = (n + 31) / 32;
-    if (g > 2147483647LL) return sqd_fail(ctx, SQD_EINVAL, "symmetric combine too large");
-    dim3 grid((unsigned)g, (unsigned)(g < 65535 ? g : 65535));
-    if (sgn > 0) k_sym_combine<1><<<grid, dim3(32, 8), 0, ctx->stream>>>(T, D, C, S, n);
-    else k_sym_combine<-1><<<grid, dim3(32, 8), 0, ctx->stream>>>(T, D, C, S, n);
-    SQD_LAUNCHED(ctx);
-    return SQD_OK;
-}
-
-// X <- (X + s X^T) / 2 in place for an n x n matrix: the block of tile pair
-// (bi, bj), bi <= bj, reads both tiles and writes the result and its mirror
-// (blocks with bi > bj have nothing to do).  Mirrored elements get the same
-// rounded sum (s = +1) or exactly opposite differences (s = -1, zero on the
-// diagonal), so the result lies exactly in the sector.
-template <int SGN>
-__global__ void k_symmetrize(double *X, int64_t n) {
-    __shared__ double a[32][33], b[32][33];
-    const int64_t bj = blockIdx.x;
-    for (int64_t bi = blockIdx.y; bi <= bj; bi += gridDim.y) {
-        const int64_t r0 = bi * 32, c0 = bj * 32;
-        for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-            const int64_t r = r0 + i, c = c0 + threadIdx.x;  // tile (bi, bj)
-            if (r < n && c < n) a[i][threadIdx.x] = X[r * n + c];
-            const int64_t r2 = c0 + i, c2 = r0 + threadIdx.x;  // tile (bj, bi)
-            if (r2 < n && c2 < n) b[i][threadIdx.x] = X[r2 * n + c2];
-        }
-        __syncthreads();
-        for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-            const int64_t r = r0 + i, c = c0 + threadIdx.x;
-            const double x = a[i][threadIdx.x], xm = b[threadIdx.x][i];
-            if (r < n && c < n) X[r * n + c] = 0.5 * (SGN > 0 ? x + xm : x - xm);
-            const int64_t r2 = c0 + i, c2 = r0 + threadIdx.x;
-            const double y = b[i][threadIdx.x], ym = a[threadIdx.x][i];
-            if (r2 < n && c2 < n) X[r2 * n + c2] = 0.5 * (SGN > 0 ? y + ym : y - ym);
-        }
-        __syncthreads();
-    }
-}
-
-int launch_symmetrize(sqd_ctx *ctx, int sgn, double *X, int64_t n) {
-    if (n == 0) return SQD_OK;
-    if (sgn != 1 && sgn != -1) return sqd_fail(ctx, SQD_EINVAL, "sector must be +1 or -1");
-    const int64_t g = (n + 31) / 32;
-    if (g > 2147483647LL) return sqd_fail(ctx, SQD_EINVAL, "symmetrisation too large");
-    dim3 grid((unsigned)g, (unsigned)(g < 65535 ? g : 65535));
-    if (sgn > 0) k_symmetrize<1><<<grid, dim3(32, 8), 0, ctx->stream>>>(X, n);
-    else k_symmetrize<-1><<<grid, dim3(32, 8), 0, ctx->stream>>>(X, n);
-    SQD_LAUNCHED(ctx);
-    return SQD_OK;
-}

@@ -134,7 +134,10 @@ __device__ __forceinline__ void same_spin_tile(const ss_args &a, int64_t row, in
 
 // One block's work of the paired-singles product: beta chunk `chunk`,
 // alpha row group `group` (dynamic shared memory: 2*AB_NA*AB_YW doubles).
-template <int EPT>
+// SKIP_HI: the caller's C is zero in every row Ja at or above the chunk's
+// last beta row (the upper-triangle input of the spin-flip product), so the
+// alpha singles with such targets are neither staged nor multiplied.
+template <int EPT, bool SKIP_HI = false>
 __device__ __forceinline__ void alpha_beta_block_t(const ab_args &a, int64_t chunk, int64_t group) {
     // double-buffered slabs in dynamic shared memory: [2][AB_NA][AB_YW] doubles
     extern __shared__ double ab_dyn[];
@@ -143,6 +146,7 @@ __device__ __forceinline__ void alpha_beta_block_t(const ab_args &a, int64_t chu
     __shared__ uint32_t sh_sa[2][AB_NA];
     __shared__ int64_t sh_row[2][AB_NA];
     __shared__ int64_t sh_off[AB_YW + 1];
+    __shared__ int sh_live[2][AB_NA];
 
     const int tid = threadIdx.x;
     const int64_t e0 = a.chunk_e[chunk], e1 = a.chunk_e[chunk + 1];
@@ -186,10 +190,12 @@ __device__ __forceinline__ void alpha_beta_block_t(const ab_args &a, int64_t chu
             sh_vrow[buf][tid] = (int64_t)a.a_pq[x] * a.norb2;
             sh_sa[buf][tid] = (a.a_sgn[x] < 0) ? 1u : 0u;
             sh_row[buf][tid] = a.a_src[x];
+            if (SKIP_HI) sh_live[buf][tid] = a.a_tgt[x] < y1;
         }
         for (int idx = tid; idx < nbat * width; idx += AB_THREADS) {
             int aa = idx / width, j = idx - aa * width;
-            cp_async8(&slab[buf][aa][j], a.C + (int64_t)a.a_tgt[x0 + aa] * a.nb + y0 + j);
+            const int64_t ja = a.a_tgt[x0 + aa];
+            if (!SKIP_HI || ja < y1) cp_async8(&slab[buf][aa][j], a.C + ja * a.nb + y0 + j);
         }
         cp_async_commit();
     };
@@ -213,6 +219,7 @@ __device__ __forceinline__ void alpha_beta_block_t(const ab_args &a, int64_t chu
         auto pairs = [&](auto km) {
             constexpr int KM = decltype(km)::value;
             for (int ai = 0; ai < nbat; ai++) {
+                if (SKIP_HI && !sh_live[buf][ai]) continue;  // a zero slab row
                 const int64_t row = sh_row[buf][ai];
                 if (row != row_cur) {
                     if (row_cur >= 0) flush(row_cur);

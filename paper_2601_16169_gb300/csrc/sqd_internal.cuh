@@ -152,6 +152,8 @@ struct sqd_tables {
     // set): the beta side of sigma is the alpha side transposed times the
     // sign; Davidson searches that sector.  0: general vectors.
     int spin_flip = 0;
+    double *scratch_h = nullptr;   // upper-triangle copy of C (spin flip)
+    double ab_upper_fmas = -1.0;   // multiply-adds of the upper-input paired singles
     bool df_ready = false;
     float2 *Vf = nullptr, *diagf = nullptr;
     double *scratch_c = nullptr;  // C as float pairs (8 bytes per element)
@@ -275,10 +277,14 @@ int launch_argmin_k(sqd_ctx *, const double *d, int64_t n, int k, int64_t *idx_d
 int launch_set_unit(sqd_ctx *, double *V, int64_t ld, int k, const int64_t *idx_dev);
 int launch_set_unit_sym(sqd_ctx *, double *V, int64_t ld, int k, const int64_t *idx_dev,
                         int64_t n, int sgn);
-// spin-flip sector pieces (n x n vectors of a shared string set, C^T = sgn C)
-int launch_sym_combine(sqd_ctx *, int sgn, const double *T, const double *D, const double *C,
-                       double *S, int64_t n);
+// spin-flip sector pieces (n x n vectors of a shared string set, C^T = sgn C;
+// k_spin_flip.cu)
+int launch_upper_half(sqd_ctx *, int sgn, const double *C, double *Ch, int64_t n);
+int launch_sym_combine(sqd_ctx *, int sgn, const double *T, const double *Y, const double *D,
+                       const double *C, double *S, int64_t n);
 int launch_symmetrize(sqd_ctx *, int sgn, double *X, int64_t n);
+int launch_alpha_beta_upper(sqd_ctx *, const sqd_tables *t, const double *Ch, double *Y);
+int alpha_beta_upper_work(sqd_ctx *, sqd_tables *t, double *fmas);
 int launch_fix_phase(sqd_ctx *, double *X, int64_t ld, int k, int64_t n, double *work_dev);
 int launch_gdk_basis(sqd_ctx *, const double *Y, int m, int m2, const double *P, int mp, int k,
                      int ldp, double *Z, int ldz, int *r_dev);
