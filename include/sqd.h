@@ -246,11 +246,14 @@ int sqd_tables_set_sigma_mode(sqd_tables *tables, int mode);
  * operators before the beta ones) an eigenstate of total spin S lies in
  * sector (-1)^S, whatever the electron count: singlets in +1, triplets in
  * -1.  On a vector of sector s the beta-beta part of sigma is
- * s times the transpose of the alpha-alpha part, so with sector s set:
- *  - sqd_sigma forms sigma = T + s T^T + H_II C + sigma_ab(C) with
- *    T = sigma_aa(C): one same-spin pass instead of two.  The caller states
- *    that every input vector lies in sector s; for any other vector the
- *    result is not H C.
+ * s times the transpose of the alpha-alpha part, and the alpha-beta part
+ * commutes with the transposition, so with sector s set:
+ *  - sqd_sigma forms sigma = (T + s T^T) + H_II C + (Y + s Y^T) with
+ *    T = sigma_aa(C) and Y = sigma_ab(Ch), Ch the upper triangle of C (half
+ *    its diagonal for s = +1): one same-spin pass instead of two and about
+ *    half of the paired singles.  The caller states that every input vector
+ *    lies in sector s; for any other vector the result is not H C.  Uses
+ *    one more scratch vector of the table's size.
  *  - sqd_davidson searches sector s: its guess vectors are the sector's unit
  *    vectors e_II or (e_IJ + s e_JI)/sqrt(2) on the lowest H_II with
  *    Ia <= Ib (Ia < Ib for s = -1), or the caller's guess projected on the
