@@ -1097,6 +1097,8 @@ def sub_spin_flip(args, local_rank, e_general=None):
            "sigma_bound": sig["bound"], "roofline": sigma_roofline(prof, args.workload),
            "kernels": class_record(prof, SIGMA_CLASSES), "clocks": clocks,
            "gpu_launches": launches}
+    # the recorded DRAM traffic is that of the general kernels, not of these
+    out["roofline"]["traffic"] = None
     if not args.no_solve:
         sr = solve_record(env, t, dict(SOLVE[args.workload]), args.workload)
         out["time_to_converged_E_s"] = sr["time_to_converged_E_s"]
