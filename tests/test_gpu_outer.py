@@ -60,7 +60,7 @@ def test_two_sqd_rounds_with_carry_over(sqd, ctx):
     h, V = torch.tensor(si.workload("h2o29", n_unique=10).h, device="cuda"), None
     w1 = si.workload("h2o29", n_unique=250)
     V = torch.tensor(w1.V, device="cuda")
-    # round 1
+    # first SQD iteration
     s1 = sqd.build_strings(ctx, dev_s(w1.raw_a), 29, 5)
     t1 = sqd.excitation_tables(ctx, 29, s1, 5, s1, 5, h, V)
     e1, X1, it1, _, _ = sqd.davidson(ctx, t1, nroots=1, tol_residual=1e-7, tol_energy=1e-10)
