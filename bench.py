@@ -441,6 +441,13 @@ def sigma_summary(prof):
 
 # ------------------------------------------------------------ records ----
 
+def _barrier():
+    """Barrier over the replicas (nothing with one process)."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
 def sigma_steps(env, t, C, S, steps, warmup):
     """Warm-up, then `steps` sigma products timed with CUDA events on the
     context's stream, the library's per-kernel events on, clocks sampled."""
@@ -448,6 +455,7 @@ def sigma_steps(env, t, C, S, steps, warmup):
     for _ in range(warmup):
         sqd.sigma(ctx, t, C, S)
     env.sync()
+    _barrier()
     ctx.profile(True)
     clk = ClockSampler(env.local_rank).start()
     ev0, ev1 = env.events()
@@ -456,6 +464,7 @@ def sigma_steps(env, t, C, S, steps, warmup):
         sqd.sigma(ctx, t, C, S)
     ev1.record(env.stream)
     env.sync()
+    _barrier()
     clocks = clk.stop()
     ms = ev0.elapsed_time(ev1)
     prof = ctx.profile_read()
@@ -710,6 +719,7 @@ def run_solve(args, rank, world, local_rank, steps=None, warmup=None, e2e_steps=
     results = [step(raw_d, h_d, V_d) for _ in range(steps)]
     ev1.record(env.stream)
     env.sync()
+    _barrier()
     clocks = clk.stop()
     dev_ms = ev0.elapsed_time(ev1)
     prof = ctx.profile_read()
@@ -785,6 +795,7 @@ def run_sigma_only(args, rank, world, local_rank):
     for _ in range(args.warmup):
         apply(ctx, t, C, S)
     env.sync()
+    _barrier()
     ctx.profile(True)
     clk = ClockSampler(local_rank).start()
     ev0, ev1 = env.events()
@@ -793,6 +804,7 @@ def run_sigma_only(args, rank, world, local_rank):
         apply(ctx, t, C, S)
     ev1.record(env.stream)
     env.sync()
+    _barrier()
     clocks = clk.stop()
     ms = ev0.elapsed_time(ev1)
     prof = ctx.profile_read()

@@ -23,6 +23,7 @@ def _worker(rank, world, port, q):
                       WORLD_SIZE=str(world))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
+    bench._barrier()                 # the barrier around every timed region
     dev_ms = 100.0 + 50.0 * rank     # rank 1 is slower
     e2e = 1.0 + rank
     work = 10.0 * (rank + 1)
@@ -56,3 +57,9 @@ def test_reference_arm_only_rank0_reports(monkeypatch):
     import bench
     args = type("A", (), dict(workload="full8", cpu_rows=100, warmup=0, steps=1))()
     assert bench.run_reference(args, 1, 2) is None
+
+
+def test_barrier_is_a_no_op_in_one_process():
+    import bench
+    assert not dist.is_initialized()
+    bench._barrier()
