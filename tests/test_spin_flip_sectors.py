@@ -34,3 +34,17 @@ def test_two_site_triplet_is_antisymmetric():
     assert abs(e[k]) <= 1e-12
     C = X[:, k].reshape(2, 2)
     assert np.max(np.abs(C + C.T)) <= 1e-12 and np.max(np.abs(C)) > 0.5
+
+
+@pytest.mark.parametrize("name,nu", [("h2o29", 40), ("scale36", 30)])
+def test_oracle_sigma_commutes_with_the_spin_flip(name, nu):
+    # a shared string set: sigma(C^T) = sigma(C)^T for any C, the identity the
+    # sector products rest on (a sign convention that treated the spins
+    # differently would break it)
+    w = si.workload(name, n_unique=nu)
+    n = w.strings_a.size
+    C = np.random.default_rng(6).standard_normal((n, n))
+    s1 = oracle.sigma(w.norb, w.h, w.V, 0.0, w.strings_a, w.strings_b, C.reshape(-1))
+    s2 = oracle.sigma(w.norb, w.h, w.V, 0.0, w.strings_a, w.strings_b, C.T.reshape(-1))
+    a, b = s1.reshape(n, n).T, s2.reshape(n, n)
+    assert np.linalg.norm(a - b) <= 1e-13 * np.linalg.norm(b)
