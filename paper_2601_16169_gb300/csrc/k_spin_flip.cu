@@ -160,6 +160,7 @@ int alpha_beta_upper_work(sqd_ctx *ctx, sqd_tables *t, double *fmas) {
     const int nch = t->ab.nchunks;
     std::vector<int32_t> tgt(A->nnz1);
     std::vector<int64_t> ce(nch + 1), cy(2 * (size_t)nch);
+    SQD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the tables are complete
     if (A->nnz1 > 0)
         SQD_CUDA(ctx, cudaMemcpy(tgt.data(), A->tgt1, sizeof(int32_t) * A->nnz1,
                                  cudaMemcpyDeviceToHost));
