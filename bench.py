@@ -767,6 +767,10 @@ def run_solve(args, rank, world, local_rank, steps=None, warmup=None, e2e_steps=
         "clocks": clocks, "gpu_launches": launches}
     if with_cpu and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(w, args.cpu_rows or default_cpu_rows(args.workload))
+        # the oracle's Davidson is its sigma products plus O(N m) vector work:
+        # the same number of products at the oracle's rate
+        out["cpu_baseline"]["solve_seconds_extrapolated"] = (hc / steps) / \
+            out["cpu_baseline"]["value"]
         rows_1t = max(1000, (args.cpu_rows or default_cpu_rows(args.workload)) // 100)
         out["cpu_baseline_1thread"] = cpu_baseline_one_thread(
             args.workload, w.ndet if w.ndet <= 10000 else rows_1t)
