@@ -665,6 +665,9 @@ def headline(args, rank, world, local_rank):
             torch.cuda.empty_cache()
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_rows or default_cpu_rows(args.workload))
+        if "solve" in line:  # the same number of sigma products at the oracle's rate
+            line["cpu_baseline"]["solve_seconds_extrapolated"] = \
+                line["solve"]["sigma_applications"] / line["cpu_baseline"]["value"]
         line["cpu_baseline_1thread"] = cpu_baseline_one_thread(args.workload, 2000)
     return line
 
