@@ -1,8 +1,11 @@
-// Spin-flip sectors of a shared string set (sqd_tables_set_spin_flip).
+// Spin-flip sectors of a shared string set (sqd_tables_set_spin_flip); not
+// in the paper, which forms the three parts of sigma (Section IV) on every
+// vector.
 //
 // With one string set for both spins the exchange (Ia, Ib) -> (Ib, Ia)
-// commutes with H: the two same-spin tables, the couplings W and the
-// diagonal are the same for both spins, and (pq|rs) = (rs|pq).  On a vector
+// commutes with the spin-free H of Section II: the two same-spin tables, the
+// couplings W and the diagonal are the same for both spins, and
+// (pq|rs) = (rs|pq).  On a vector
 // of one sector, C^T = s C with s = +1 or -1:
 //  - the beta side of sigma is s times the transposed alpha side;
 //  - the paired-singles part commutes with the transposition too,
